@@ -1,0 +1,98 @@
+"""Pins for oracle/estimator.py (Alg. 1 and Alg. 2).
+
+* Unbiasedness by exact enumeration: n = 6, k = 2, l = 1 gives 2^8 sign patterns;
+  with exact solves, the mean of the stochastic log-det term equals
+  tr(log(P^-1/2 K_hat P^-1/2)) = log det K_hat - log det P_hat (Lemma
+  "Decomposition of the log-determinant"), and the mean of the trace estimate
+  equals tr(K_hat^-1 dK_hat_p) for every p, to rounding.  The literal Alg. 1
+  (normalised probes, no rho0 scaling) fails the same identity.
+* k = n: P_hat = K_hat, so the stochastic terms vanish and the estimator returns the
+  exact MLL and gradient.
+* k = 0: P_hat = sigma^2 I and the estimator is the classical SLQ estimator.
+* Against the exact values, the estimate lies within 4 standard errors.
+* With a 1-D RBF kernel, a rank-30 preconditioner cuts the variance of the
+  log-det estimate by orders of magnitude (qualitative reading of Tab. S1).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import estimator, exact, kernels
+from paper_2107_00243_gb300 import workloads
+
+
+def _enumerate(p, k, literal=False):
+    n = p.n
+    acc_stoch, acc_trace = 0.0, 0.0
+    count = 0
+    for bits in itertools.product([-1.0, 1.0], repeat=k + n):
+        e1 = np.array(bits[:k])[:, None]
+        e2 = np.array(bits[k:])[:, None]
+        out = estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, k, 1, 1e-15, 60,
+                                     eps=(e1, e2), literal=literal)
+        acc_stoch = acc_stoch + out["stoch"]
+        acc_trace = acc_trace + out["trace_p"] - out["trP_p"]
+        count += 1
+    return acc_stoch / count, acc_trace / count, out
+
+
+@pytest.mark.parametrize("kind", [kernels.RBF, kernels.MATERN32])
+def test_unbiased_by_enumeration(kind):
+    p = workloads.random_problem(6, 2, kind=kind, seed=11, s2=0.1)
+    ex = exact.exact_mll_and_grad(kind, p.X, p.y, p.theta, p.ard)
+    mean_stoch, mean_probe, last = _enumerate(p, 2)
+    target = ex["logdet"] - last["logdetP"]
+    assert abs(mean_stoch - target) < 1e-10 * max(1.0, abs(target)), (mean_stoch, target)
+    np.testing.assert_allclose(mean_probe + last["trP_p"], ex["trace_p"], rtol=1e-9, atol=1e-9)
+
+
+def test_literal_reading_is_biased():
+    p = workloads.random_problem(6, 2, kind=kernels.RBF, seed=11, s2=0.1)
+    ex = exact.exact_mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard)
+    mean_stoch, _, last = _enumerate(p, 2, literal=True)
+    target = ex["logdet"] - last["logdetP"]
+    assert abs(mean_stoch - target) > 1e-3 * max(1.0, abs(target))
+
+
+@pytest.mark.parametrize("kind", kernels.KINDS)
+def test_full_rank_preconditioner_gives_exact_values(kind):
+    p = workloads.random_problem(40, 2, kind=kind, seed=12, s2=0.05, lo=1.0, hi=2.0)
+    ex = exact.exact_mll_and_grad(kind, p.X, p.y, p.theta, p.ard)
+    est = estimator.mll_and_grad(kind, p.X, p.y, p.theta, p.ard, 40, 3, 1e-12, 100)
+    if est["rank"] < 40:
+        pytest.skip("numerically rank deficient")
+    assert abs(est["stoch"]) < 1e-8
+    assert abs(est["mll"] - ex["mll"]) < 1e-8 * abs(ex["mll"])
+    np.testing.assert_allclose(est["grad"], ex["grad"], rtol=1e-6, atol=1e-6)
+
+
+def test_rank_zero_is_classical_slq():
+    p = workloads.random_problem(80, 2, kind=kernels.RBF, seed=13, s2=0.2)
+    est = estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, 0, 4, 1e-12, 200)
+    # classical SLQ with Rademacher e: log det K = n log s2 + tr log(K / s2),
+    # e^T log(K/s2) e by dense eigendecomposition
+    Kh = kernels.khat_dense(p.kind, p.X, p.theta, p.ard)
+    lam, V = np.linalg.eigh(Kh / p.theta[-1])
+    from oracle import probes
+    _, e2 = probes.eps_pair(0, 0, 80, 4)
+    vals = [(e @ V) ** 2 @ np.log(lam) for e in e2.T]
+    assert abs(est["logdetP"] - 80 * np.log(p.theta[-1])) < 1e-9
+    assert abs(est["stoch"] - np.mean(vals)) < 1e-7 * abs(np.mean(vals))
+
+
+def test_estimate_within_statistical_bound():
+    p = workloads.random_problem(300, 2, kind=kernels.MATERN32, seed=14, s2=0.05)
+    ex = exact.exact_mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard)
+    est = estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, 10, 64, 1e-10, 300, seed=3)
+    se = np.std(est["gamma"], ddof=1) / np.sqrt(64)
+    assert abs(est["logdet"] - ex["logdet"]) <= 4 * se + 1e-8
+
+
+def test_preconditioning_reduces_variance():
+    p = workloads.random_problem(400, 1, kind=kernels.RBF, seed=15, s2=0.01, lo=0.2, hi=0.2)
+    def var_of(k):
+        vals = [estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, k, 4, 1e-10, 400,
+                                       seed=s, with_grad=False)["logdet"] for s in range(8)]
+        return np.var(vals)
+    assert var_of(30) * 100 < var_of(0)
