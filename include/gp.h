@@ -1,0 +1,207 @@
+/*
+ * gp.h -- C ABI of the GB300 (sm_103a) preconditioned GP log-marginal-likelihood library.
+ *
+ * The library evaluates the stochastic estimator of Wenger et al., "Preconditioning
+ * for Scalable Gaussian Process Hyperparameter Optimization" (ICML 2022):
+ *   Alg. 1  log-marginal likelihood L(theta) = -1/2 (y^T K^-1 y + log det K + n log 2 pi)
+ *   Alg. 2  its gradient dL/dtheta (eq. derivative_likelihood)
+ * with K_hat = K + sigma^2 I (Sec. 2.1), a rank-k pivoted-Cholesky preconditioner
+ * P_hat = sigma^2 I + L L^T applied through the matrix inversion lemma (Sec. 2.2),
+ * preconditioned CG on [y, z_1..z_l] with Lanczos tridiagonals taken from the CG
+ * coefficients (Sec. S1.2, footnote to Sec. 4.4), and the variance-reduced trace
+ * estimators of eqs. (logdet-decomposition) and (logdet-decomposition_deriv).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers are DEVICE pointers owned by the caller unless marked "host".  The
+ *   library never allocates device memory: scratch comes from the caller's
+ *   workspace `ws` of at least gp_workspace_size(...) bytes (256-byte aligned).
+ * - Real arrays (X, y, V, W, L, B, ...) hold double when the problem's precision
+ *   is GP_FP64 and float otherwise.  theta and all scalar outputs are double.
+ * - X is n x d row-major.  Blocks of vectors (V, W, L, B, ...) are column-major
+ *   with a leading dimension >= n.
+ * - Arguments are validated on the host before anything is launched; an invalid
+ *   call returns GP_ERR_INVALID_ARG (or GP_ERR_WORKSPACE) and launches nothing.
+ *   gp_last_error_message() then describes the problem.
+ * - Work is enqueued on `stream` (NULL = the legacy default stream).  Functions
+ *   marked "asynchronous" return after enqueueing; device-side conditions are
+ *   written to device status words.  gp_mbcg and gp_mll_and_grad poll the
+ *   device for CG convergence and therefore synchronise with `stream`; they
+ *   return the final status, including device-side conditions.
+ * - Limits: 1 <= d <= 32, 0 <= k <= min(n, 2048), 1 <= t <= 1024, n < 2^31.
+ * - Errors: negative gp_status values; positive values are warnings with full
+ *   results written.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gp_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  GP_OK = 0,
+  GP_WARN_NOT_CONVERGED = 1,   /* a CG column hit max_iter before the tolerance   */
+  GP_WARN_RANK_DEFICIENT = 2,  /* pivoted Cholesky stopped below the requested k   */
+  GP_ERR_INVALID_ARG = -1,
+  GP_ERR_CUDA = -2,
+  GP_ERR_NOT_SPD = -3,         /* Woodbury core or a tridiagonal lost definiteness */
+  GP_ERR_WORKSPACE = -4,
+  GP_ERR_DEVICE_TIMEOUT = -5,  /* an iteration cap in device code was reached      */
+  GP_ERR_NUMERIC = -6          /* NaN/Inf or a CG breakdown (p^T K p <= 0)         */
+} gp_status;
+
+/* Sec. 5 "Experimental Setup": RBF and Matern kernels with output scale s = k(x,x),
+ * lengthscales l_j and noise sigma^2.  r^2 = sum_j ((x_j - x'_j)/l_j)^2 and
+ *   RBF       s exp(-r^2/2)
+ *   MATERN32  s (1 + sqrt3 r) exp(-sqrt3 r)
+ *   MATERN52  s (1 + sqrt5 r + 5r^2/3) exp(-sqrt5 r)                              */
+typedef enum { GP_RBF = 0, GP_MATERN32 = 3, GP_MATERN52 = 5 } gp_kernel_kind;
+
+/* Storage and arithmetic of a problem.
+ *   GP_FP64  everything in double (kernel MVMs on the FP64 pipe)
+ *   GP_FP32  float vectors, kernel MVMs on CUDA-core FP32 FMAs
+ *   GP_TF32  float vectors, kernel-MVM tiles on tcgen05 tensor cores in TF32
+ *   GP_BF16  float vectors, kernel-MVM tiles on tcgen05 tensor cores in BF16
+ * FP64 is always used for pivot selection, the k x k Woodbury core, the Lanczos
+ * tridiagonal eigenproblems and the final sums.                                   */
+typedef enum { GP_FP64 = 0, GP_FP32 = 1, GP_TF32 = 2, GP_BF16 = 3 } gp_precision;
+
+typedef struct {
+  int64_t n;            /* number of training points                           */
+  int32_t d;            /* input dimension                                     */
+  int32_t kind;         /* gp_kernel_kind                                      */
+  int32_t ard;          /* 1: one lengthscale per dimension (D = d); 0: D = 1  */
+  int32_t precision;    /* gp_precision: element type of every real array      */
+  const void* X;        /* device, n x d row-major                             */
+  const double* theta;  /* device, p = D + 2 values [l_1..l_D, s, sigma^2]     */
+} gp_problem;
+
+typedef struct {
+  double cg_tol;           /* stop a column when ||r||_2 <= cg_tol ||b||_2        */
+  int32_t max_iter;        /* CG iteration cap per column (>= 1)                  */
+  int32_t recompute_every; /* r = b - K_hat x every R iterations (0 = never)      */
+  uint64_t seed;           /* probe seed (counter-based SplitMix64 hash)          */
+  double pivchol_tol;      /* stop pivoted Cholesky when tr(K - LL^T) <= tol tr K */
+  int32_t check_every;     /* host polls CG convergence every this many steps (0 = 4) */
+  int32_t reserved;
+} gp_opts;
+
+/* Which entry point a workspace query is for. */
+typedef enum {
+  GP_FN_KERNEL_MVM = 0,
+  GP_FN_KERNEL_GRAD_MVM = 1,
+  GP_FN_PIVCHOL = 2,
+  GP_FN_MBCG = 3,
+  GP_FN_MLL_AND_GRAD = 4
+} gp_fn;
+
+/* Bytes of workspace entry point `fn` needs for a problem of n points in d
+ * dimensions, preconditioner rank k, t right-hand-side columns (for
+ * GP_FN_MLL_AND_GRAD: t = n_probes + 1), precision and CG cap max_iter.         */
+size_t gp_workspace_size(int32_t fn, int64_t n, int32_t d, int32_t k, int32_t t,
+                         int32_t precision, int32_t max_iter);
+
+/* Kernel-matrix block product (the inner operation of CG, Sec. 2.2):
+ *   W = (K + sigma^2 I) V,   V, W: n x t column-major (leading dims ldv, ldw).
+ * K is never formed: each tile evaluates the kernel and multiplies it into V.
+ * W must not alias V.  Asynchronous.                                              */
+gp_status gp_kernel_mvm(const gp_problem* prob, const void* V, int64_t ldv, int32_t t,
+                        void* W, int64_t ldw, void* ws, size_t ws_bytes,
+                        gp_stream_t stream);
+
+/* Derivative products for every hyperparameter (eq. derivative_likelihood needs
+ * dK_hat/dtheta):  dW_q = dK_hat/dtheta_q V  for q = 0..p-1 in the order
+ * [l_1..l_D, s, sigma^2]; block q starts at element q * ldw * t of dW and is
+ * n x t column-major with leading dim ldw.  Asynchronous.                         */
+gp_status gp_kernel_grad_mvm(const gp_problem* prob, const void* V, int64_t ldv, int32_t t,
+                             void* dW, int64_t ldw, void* ws, size_t ws_bytes,
+                             gp_stream_t stream);
+
+/* Greedy rank-k partial pivoted Cholesky of the noise-free K (Prop. "Cholesky
+ * approximation quality", after Harbrecht et al. 2012):
+ *   pi_m = argmax of the residual diagonal (lowest index on ties, FP64),
+ *   L[:, m] = (K[:, pi_m] - L[:, :m] L[pi_m, :m]^T) / sqrt(d_{pi_m}).
+ * Stops early when the residual trace <= tol * tr K or the best residual <= 0.
+ * Outputs: L (n x k column-major, ld ldl; columns >= rank are zero), piv (k int32,
+ * entries >= rank are -1), rank_out (1 int32).  piv_override (device, k int32, or
+ * NULL) forces the pivot order.  Asynchronous.                                    */
+gp_status gp_pivchol(const gp_problem* prob, int32_t k, double tol,
+                     const int32_t* piv_override, void* L, int64_t ldl, int32_t* piv,
+                     int32_t* rank_out, void* ws, size_t ws_bytes, gp_stream_t stream);
+
+/* Preconditioned CG on t right-hand sides at once (footnote to Sec. 4.4) with
+ * P_hat = sigma^2 I + L L^T (L: n x k, ld ldl, the first k columns are used):
+ *   per column: x_0 = 0, alpha_j = rho_j / p^T K_hat p, beta_j = rho_{j+1} / rho_j,
+ *   stop when ||r|| <= cg_tol ||b|| or at max_iter (iters_override: device t int32
+ *   caps, or NULL), true residual every recompute_every steps.
+ * Outputs: Xsol (n x t, ld ldx) ~ K_hat^-1 B; PinvB (n x t, ld ldx, or NULL) =
+ * P_hat^-1 B; the Lanczos tridiagonals from the CG coefficients (Sec. S1.2):
+ * T_diag[c * max_iter + j] = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+ * T_off[c * max_iter + j] = sqrt(beta_j)/alpha_j; rho0[c] = b^T P^-1 b;
+ * iters[c] = steps taken; status (1 int32).  Synchronises with `stream`.         */
+gp_status gp_mbcg(const gp_problem* prob, const void* L, int64_t ldl, int32_t k,
+                  const void* B, int64_t ldb, int32_t t, const int32_t* iters_override,
+                  void* Xsol, int64_t ldx, void* PinvB, double* T_diag, double* T_off,
+                  double* rho0, int32_t* iters, int32_t* status, const gp_opts* opts,
+                  void* ws, size_t ws_bytes, gp_stream_t stream);
+
+/* Output layout of gp_mll_and_grad (double, device).  p = D + 2, l = n_probes. */
+#define GP_OUT_MLL 0      /* estimate of L(theta)                                   */
+#define GP_OUT_QUAD 1     /* y^T u, u ~ K_hat^-1 y                                  */
+#define GP_OUT_LOGDETP 2  /* log det P_hat (determinant lemma)                      */
+#define GP_OUT_STOCH 3    /* (1/l) sum_i gamma_i ~ log det K_hat - log det P_hat    */
+#define GP_OUT_LOGDET 4   /* GP_OUT_LOGDETP + GP_OUT_STOCH                          */
+#define GP_OUT_HEAD 8
+#define GP_OUT_GRAD(p) (GP_OUT_HEAD)                 /* p entries: dL/dtheta      */
+#define GP_OUT_GK(p) (GP_OUT_HEAD + (p))             /* p: 1/2 u^T dK u - (1/2l) sum_i (K^-1 z_i)^T dK (P^-1 z_i) */
+#define GP_OUT_PROBEP(p) (GP_OUT_HEAD + 2 * (p))     /* p: (1/l) sum_i (P^-1 z_i)^T dP (P^-1 z_i) */
+#define GP_OUT_TRP(p) (GP_OUT_HEAD + 3 * (p))        /* p: tr(P_hat^-1 dP_hat)    */
+#define GP_OUT_GAMMA(p) (GP_OUT_HEAD + 4 * (p))      /* l: gamma_i                */
+#define GP_OUT_LEN(p, l) (GP_OUT_HEAD + 4 * (p) + (l))
+/* Integer output layout (int32, device). t = n_probes + 1.                        */
+#define GP_IOUT_STATUS 0
+#define GP_IOUT_RANK 1
+#define GP_IOUT_ITERS 2                              /* t entries                 */
+#define GP_IOUT_PIV(t) (2 + (t))                     /* k entries                 */
+#define GP_IOUT_LEN(k, t) (2 + (t) + (k))
+
+/* The whole estimator (Alg. 1 and Alg. 2 in one CG call):
+ *   pivoted Cholesky -> Woodbury core and log det P_hat -> probes
+ *   z_i = L eps1_i + sigma eps2_i (covariance P_hat) -> CG on [y, z_1..z_l]
+ *   -> gamma_i = rho0_i e1^T log(T_i) e1 -> gradient contraction with dK_hat
+ *   -> tr(P_hat^-1 dP_hat) (eq. preconditioner_trace) and the probe terms with
+ *   dP_hat at frozen pivots -> assembly:
+ *   mll = -1/2 (y^T u + log det P_hat + (1/l) sum gamma_i + n log 2 pi)
+ *   grad = GK + 1/2 PROBEP - 1/2 TRP.
+ * y: n reals.  eps_override (device, (k + n) x n_probes int8 +-1 column-major with
+ * leading dim k + n: rows 0..k-1 eps1, rows k.. eps2; or NULL = SplitMix64 from
+ * opts->seed), piv_override (k int32 or NULL), iters_override (t int32 or NULL)
+ * exist for parity testing.  out: GP_OUT_LEN(p, n_probes) doubles; iout:
+ * GP_IOUT_LEN(k, t) int32.  Synchronises with `stream`.                          */
+gp_status gp_mll_and_grad(const gp_problem* prob, const void* y, int32_t k,
+                          int32_t n_probes, const int8_t* eps_override,
+                          const int32_t* piv_override, const int32_t* iters_override,
+                          double* out, int32_t* iout, const gp_opts* opts, void* ws,
+                          size_t ws_bytes, gp_stream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* gp_status_string(int32_t status);
+
+/* Detail of the last host-side validation failure on this thread (static storage). */
+const char* gp_last_error_message(void);
+
+/* Rademacher signs of the probe generator, for inspection:
+ * out[c * rows + r] = +-1 for stream 1 (eps1) or 2 (eps2).  Asynchronous.         */
+gp_status gp_rademacher(uint64_t seed, int32_t stream_id, int64_t rows, int32_t cols,
+                        int8_t* out, gp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H */

@@ -1,0 +1,657 @@
+// C ABI entry points (include/gp.h): argument validation, workspace planning and
+// the order of the estimator's steps (Alg. 1 and Alg. 2 fused into one CG call).
+#include <cstdarg>
+#include <algorithm>
+
+#include "ops.h"
+
+namespace gp {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+const char* last_error() { return g_err; }
+
+namespace {
+
+size_t elem_size(int prec) { return prec == GP_FP64 ? sizeof(double) : sizeof(float); }
+
+gp_status check_problem(const gp_problem* prob, bool need_data = true) {
+  GP_REQUIRE(prob != nullptr, "problem is NULL");
+  GP_REQUIRE(prob->n >= 1 && prob->n < (int64_t(1) << 31), "n=%lld out of range [1, 2^31)",
+             (long long)prob->n);
+  GP_REQUIRE(prob->d >= 1 && prob->d <= kMaxD, "d=%d out of range [1, %d]", prob->d, kMaxD);
+  GP_REQUIRE(prob->kind == GP_RBF || prob->kind == GP_MATERN32 || prob->kind == GP_MATERN52,
+             "unknown kernel kind %d", prob->kind);
+  GP_REQUIRE(prob->precision >= GP_FP64 && prob->precision <= GP_BF16, "unknown precision %d",
+             prob->precision);
+  if (need_data) {
+    GP_REQUIRE(prob->X != nullptr, "X is NULL");
+    GP_REQUIRE(prob->theta != nullptr, "theta is NULL");
+  }
+  return GP_OK;
+}
+
+Prob make_prob(const gp_problem* p) {
+  Prob pb;
+  pb.n = p->n;
+  pb.d = p->d;
+  pb.kind = p->kind;
+  pb.ard = p->ard ? 1 : 0;
+  pb.D = pb.ard ? pb.d : 1;
+  pb.p = pb.D + 2;
+  pb.prec = p->precision;
+  pb.X = p->X;
+  pb.theta = p->theta;
+  return pb;
+}
+
+// ---- workspace plans ---------------------------------------------------------------
+struct PrepPlan {
+  PrepBufs pr;
+};
+void plan_prep(Arena& A, const Prob& pb, PrepPlan& P) {
+  P.pr.Xs = A.take<char>(elem_size(pb.prec) * (size_t)pb.n * pb.d);
+  P.pr.mean = A.take<double>(kMaxD);
+  P.pr.part = A.take<double>((size_t)kPrepBlocks * kMaxD);
+  P.pr.counter = A.take<unsigned>(4);
+}
+
+struct MvmPlan {
+  PrepPlan prep;
+  void* scratch;     // SIMT split partials
+  TcBufs tc;
+  bool use_tc;
+};
+void plan_mvm(Arena& A, const Prob& pb, int t, MvmPlan& P) {
+  plan_prep(A, pb, P.prep);
+  P.use_tc = (pb.prec == GP_BF16 || pb.prec == GP_TF32);
+  P.scratch = nullptr;
+  P.tc = TcBufs{};
+  if (P.use_tc) {
+    P.tc.xpack = A.take<char>(tc_xpack_bytes(pb.n, pb.d, pb.prec));
+    P.tc.norms = A.take<float>((size_t)pb.n);
+    P.tc.vpack = A.take<char>(tc_vpack_bytes(pb.n, t, pb.prec));
+    P.tc.part = A.take<float>(tc_part_elems(pb.n, t));
+  } else {
+    P.scratch = A.take<char>(elem_size(pb.prec) * simt_scratch_elems(pb.n, t));
+  }
+}
+
+struct PivPlan {
+  PivBufs b;
+};
+void plan_piv(Arena& A, const Prob& pb, int k, PivPlan& P) {
+  P.b.dres = A.take<double>((size_t)pb.n);
+  P.b.pval = A.take<double>(kPivBlocks);
+  P.b.pidx = A.take<int>(kPivBlocks);
+  P.b.psum = A.take<double>(kPivBlocks);
+  P.b.dval = A.take<double>((size_t)k + 2);
+  P.b.trace0 = A.take<double>(1);
+  P.b.stop = A.take<int>(1);
+  P.b.counter = A.take<unsigned>(4);
+}
+
+template <class T>
+void plan_cg(Arena& A, const Prob& pb, int k, int t, int max_iter, CgBufs<T>& c) {
+  const size_t nt = (size_t)pb.n * t;
+  c.X = A.take<T>(nt);
+  c.R = A.take<T>(nt);
+  c.Z = A.take<T>(nt);
+  c.P = A.take<T>(nt);
+  c.Q = A.take<T>(nt);
+  c.Sp = A.take<T>((size_t)std::max(k, 1) * t);
+  c.atb_part = A.take<double>((size_t)atb_chunks(pb.n) * std::max(k, 1) * t);
+  c.S = A.take<double>((size_t)std::max(k, 1) * t);
+  c.rho = A.take<double>(t);
+  c.rho0 = A.take<double>(t);
+  c.bnorm2 = A.take<double>(t);
+  c.alpha = A.take<double>((size_t)t * max_iter);
+  c.beta = A.take<double>((size_t)t * max_iter);
+  c.part = A.take<double>((size_t)t * kCgBlocks);
+  c.active = A.take<int>(t);
+  c.caps = A.take<int>(t);
+  c.iters = A.take<int>(t);
+  c.n_active = A.take<int>(1);
+  c.status = A.take<int>(1);
+  c.counter = A.take<unsigned>(4);
+}
+
+struct CorePlan {
+  double *G, *Cfac, *Cinv, *work, *atb_part, *logdet;
+};
+void plan_core(Arena& A, const Prob& pb, int k, CorePlan& P) {
+  size_t kk = (size_t)std::max(k, 1) * std::max(k, 1);
+  P.G = A.take<double>(kk);
+  P.Cfac = A.take<double>(kk);
+  P.Cinv = A.take<double>(kk);
+  P.work = A.take<double>(kk);
+  P.atb_part = A.take<double>((size_t)atb_chunks(pb.n) * kk);
+  P.logdet = A.take<double>(1);
+}
+
+void plan_prec(Arena& A, const Prob& pb, int k, int nl, PrecBufs& b) {
+  size_t K = std::max(k, 1), kb = K + nl;
+  b.Q = A.take<double>((size_t)(pb.p - 1) * K * kb);
+  b.dW = A.take<double>((size_t)(pb.p - 1) * K * K);
+  b.Lpi = A.take<double>(K * K);
+  b.Lpinv = A.take<double>(K * K);
+  b.A1 = A.take<double>(K * K);
+  b.B1 = A.take<double>(K * K);
+  b.tmp = A.take<double>(K * K);
+  b.LtW = A.take<double>(K * std::max(nl, 1) + 512);
+  b.Cv = A.take<double>(K * std::max(nl, 1));
+  b.part = A.take<double>((size_t)atb_chunks(pb.n) * K * kb);
+}
+
+// ---- matrix-vector products used by CG ----------------------------------------------
+template <class T>
+struct SimtMvm : MvmOp {
+  Prob pb;
+  const void* Xs;
+  void* scratch;
+  gp_status apply(const void* V, int64_t ldv, int t, void* W, int64_t ldw, const int* gate,
+                  cudaStream_t st) override {
+    return kmvm_simt<T>(pb, Xs, V, ldv, t, W, ldw, scratch, gate, st);
+  }
+};
+
+struct TcMvm : MvmOp {
+  Prob pb;
+  TcBufs tb;
+  gp_status apply(const void* V, int64_t ldv, int t, void* W, int64_t ldw, const int* gate,
+                  cudaStream_t st) override {
+    return kmvm_tc(pb, tb, static_cast<const float*>(V), ldv, t, static_cast<float*>(W), ldw,
+                   gate, st);
+  }
+};
+
+template <class T>
+gp_status run_prep(const Prob& pb, const PrepPlan& P, cudaStream_t st) {
+  GP_CUDA_TRY(cudaMemsetAsync(P.pr.counter, 0, 4 * sizeof(unsigned), st));
+  return prep_inputs<T>(pb, P.pr, st);
+}
+
+template <class T>
+gp_status run_kernel_mvm(const Prob& pb, const void* V, int64_t ldv, int t, void* W, int64_t ldw,
+                         MvmPlan& P, cudaStream_t st) {
+  GP_TRY(run_prep<T>(pb, P.prep, st));
+  if (P.use_tc) {
+    GP_TRY(tc_prepare_inputs(pb, P.prep.pr.Xs, P.tc, st));
+    TcMvm op;
+    op.pb = pb;
+    op.tb = P.tc;
+    return op.apply(V, ldv, t, W, ldw, nullptr, st);
+  }
+  SimtMvm<T> op;
+  op.pb = pb;
+  op.Xs = P.prep.pr.Xs;
+  op.scratch = P.scratch;
+  return op.apply(V, ldv, t, W, ldw, nullptr, st);
+}
+
+// ---- small kernels for the assembly ---------------------------------------------------
+__global__ void fill_weights(int t, double* w) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= t) return;
+  // column 0: (u, u) with 1/2; probe columns: (K^-1 z_i, P^-1 z_i) with -1/(2l)
+  w[c] = (c == 0) ? 0.5 : -0.5 / (double)(t - 1);
+}
+
+__global__ void assemble(int64_t n, int P, int nl, int k, const int* rank, const int* iters,
+                         const int* piv, const int* dev_status, const int* rank_stat,
+                         double* out, int* iout) {
+  if (threadIdx.x != 0) return;
+  const double LOG2PI = 1.8378770664093453;
+  double stoch = 0.0;
+  for (int i = 0; i < nl; ++i) stoch += out[GP_OUT_GAMMA(P) + i];
+  stoch = nl > 0 ? stoch / nl : 0.0;
+  out[GP_OUT_STOCH] = stoch;
+  out[GP_OUT_LOGDET] = out[GP_OUT_LOGDETP] + stoch;
+  out[GP_OUT_MLL] = -0.5 * (out[GP_OUT_QUAD] + out[GP_OUT_LOGDET] + (double)n * LOG2PI);
+  for (int q = 0; q < P; ++q)
+    out[GP_OUT_GRAD(P) + q] = out[GP_OUT_GK(P) + q] + 0.5 * out[GP_OUT_PROBEP(P) + q] -
+                              0.5 * out[GP_OUT_TRP(P) + q];
+  for (int h = 5; h < GP_OUT_HEAD; ++h) out[h] = 0.0;
+  const int t = nl + 1;
+  iout[GP_IOUT_STATUS] = *dev_status;
+  iout[GP_IOUT_RANK] = *rank;
+  for (int c = 0; c < t; ++c) iout[GP_IOUT_ITERS + c] = iters[c];
+  for (int m = 0; m < k; ++m) iout[GP_IOUT_PIV(t) + m] = piv[m];
+  (void)rank_stat;
+}
+
+template <class T>
+__global__ void copy_col(int64_t n, const T* src, T* dst) {
+  int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a < n) dst[a] = src[a];
+}
+
+// ---- gp_mll_and_grad plan -----------------------------------------------------------
+template <class T>
+struct MllPlan {
+  MvmPlan mvm;
+  PivPlan piv;
+  CorePlan core;
+  CgBufs<T> cg;
+  PrecBufs prec;
+  T* L;
+  int* pivots;
+  int* rank;
+  T* B;
+  T* PinvB;
+  double* wts;
+  double* part;
+  unsigned* counter;
+  int* status;
+};
+template <class T>
+void plan_mll(Arena& A, const Prob& pb, int k, int nl, int max_iter, MllPlan<T>& P) {
+  const int t = nl + 1;
+  plan_mvm(A, pb, t, P.mvm);
+  plan_piv(A, pb, k, P.piv);
+  plan_core(A, pb, k, P.core);
+  plan_cg<T>(A, pb, k, t, max_iter, P.cg);
+  plan_prec(A, pb, k, nl, P.prec);
+  P.L = A.take<T>((size_t)pb.n * std::max(k, 1));
+  P.pivots = A.take<int>(std::max(k, 1));
+  P.rank = A.take<int>(1);
+  P.B = A.take<T>((size_t)pb.n * t);
+  P.PinvB = A.take<T>((size_t)pb.n * t);
+  P.wts = A.take<double>(t);
+  P.part = A.take<double>(std::max<size_t>(contract_part_elems(pb.n), 4 * kCgBlocks));
+  P.counter = A.take<unsigned>(4);
+  P.status = A.take<int>(1);
+}
+
+template <class T>
+gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
+                   const int* piv_override, const int* iters_override, double* out, int* iout,
+                   const gp_opts& o, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const int t = nl + 1;
+  MllPlan<T> P;
+  {
+    Arena dry;
+    plan_mll<T>(dry, pb, k, nl, o.max_iter, P);
+    if (dry.off > ws_bytes) {
+      set_error("workspace too small: need %zu bytes, got %zu", dry.off, ws_bytes);
+      return GP_ERR_WORKSPACE;
+    }
+  }
+  Arena A;
+  A.base = static_cast<char*>(ws);
+  plan_mll<T>(A, pb, k, nl, o.max_iter, P);
+
+  GP_CUDA_TRY(cudaMemsetAsync(P.counter, 0, 4 * sizeof(unsigned), st));
+  GP_CUDA_TRY(cudaMemsetAsync(P.piv.b.counter, 0, 4 * sizeof(unsigned), st));
+  GP_CUDA_TRY(cudaMemsetAsync(P.cg.counter, 0, 4 * sizeof(unsigned), st));
+  GP_CUDA_TRY(cudaMemsetAsync(P.cg.status, 0, sizeof(int), st));
+  GP_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * GP_OUT_LEN(pb.p, nl), st));
+
+  // S1: scaled inputs
+  GP_TRY(run_prep<T>(pb, P.mvm.prep, st));
+  const void* Xs = P.mvm.prep.pr.Xs;
+  // S2: pivoted Cholesky
+  GP_TRY(pivchol_run<T>(pb, Xs, k, o.pivchol_tol, piv_override, P.L, pb.n, P.pivots, P.rank,
+                        P.piv.b, st));
+  // S3: Woodbury core and log det P_hat
+  if (k > 0) GP_TRY(atb<T>(pb.n, P.L, pb.n, k, P.L, pb.n, k, P.core.atb_part, P.core.G, st));
+  GP_TRY(woodbury_core(k, P.core.G, pb.theta, pb.D, pb.n, P.core.Cfac, P.core.Cinv, P.core.work,
+                       out + GP_OUT_LOGDETP, P.cg.status, st));
+  // S4: probes, B = [y, z_1..z_l]
+  GP_TRY(make_rhs<T>(pb, y, P.L, pb.n, k, nl, o.seed, eps, P.B, pb.n, st));
+  // S5-S7: mBCG
+  int host_status = 0;
+  if (P.mvm.use_tc) {
+    GP_TRY(tc_prepare_inputs(pb, Xs, P.mvm.tc, st));
+    TcMvm op;
+    op.pb = pb;
+    op.tb = P.mvm.tc;
+    GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o, P.cg,
+                       P.PinvB, pb.n, &host_status, st));
+  } else {
+    SimtMvm<T> op;
+    op.pb = pb;
+    op.Xs = Xs;
+    op.scratch = P.mvm.scratch;
+    GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o, P.cg,
+                       P.PinvB, pb.n, &host_status, st));
+  }
+  // S8: Lanczos quadrature per probe
+  GP_TRY(lanczos_logquad(nl, 1, o.max_iter, P.cg.alpha, P.cg.beta, P.cg.iters, P.cg.rho0,
+                         out + GP_OUT_GAMMA(pb.p), P.cg.status, st));
+  // quadratic term y^T u
+  GP_TRY(dot_into<T>(pb.n, y, P.cg.X, P.part, P.counter, out + GP_OUT_QUAD, st));
+  // S9: gradient contraction with A = [u, K^-1 z_i], B = [u, P^-1 z_i]
+  copy_col<T><<<(unsigned)cdiv(pb.n, 256), 256, 0, st>>>(pb.n, P.cg.X, P.PinvB);
+  GP_LAUNCH_CHECK();
+  fill_weights<<<(unsigned)cdiv(t, 128), 128, 0, st>>>(t, P.wts);
+  GP_LAUNCH_CHECK();
+  GP_TRY(contract_simt<T>(pb, Xs, P.cg.X, pb.n, P.PinvB, pb.n, P.wts, t, P.part, P.counter,
+                          out + GP_OUT_GK(pb.p), st));
+  // S10: preconditioner terms with W = P^-1 z_i (columns 1..l of PinvB)
+  GP_TRY(precond_terms<T>(pb, Xs, P.L, pb.n, k, P.pivots, P.rank, P.PinvB + pb.n, pb.n, nl,
+                          P.core.Cinv, P.prec, out + GP_OUT_TRP(pb.p), out + GP_OUT_PROBEP(pb.p),
+                          st));
+  // S11: assembly
+  assemble<<<1, 32, 0, st>>>(pb.n, pb.p, nl, k, P.rank, P.cg.iters, P.pivots, P.cg.status,
+                             nullptr, out, iout);
+  GP_LAUNCH_CHECK();
+
+  int hstat = 0, hrank = 0;
+  GP_CUDA_TRY(cudaMemcpyAsync(&hstat, P.cg.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GP_CUDA_TRY(cudaMemcpyAsync(&hrank, P.rank, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GP_CUDA_TRY(cudaStreamSynchronize(st));
+  GP_CUDA_TRY(cudaGetLastError());
+  if (hstat < 0) return (gp_status)hstat;
+  if (hrank < k) return GP_WARN_RANK_DEFICIENT;
+  return GP_OK;
+}
+
+template <class T>
+gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, int64_t ldb,
+                    int t, const int* iters_override, T* Xsol, int64_t ldx, T* PinvB,
+                    double* T_diag, double* T_off, double* rho0, int* iters, int* status,
+                    const gp_opts& o, void* ws, size_t ws_bytes, cudaStream_t st);
+
+}  // namespace
+}  // namespace gp
+
+using namespace gp;
+
+// ---- workspace sizes --------------------------------------------------------------------
+extern "C" size_t gp_workspace_size(int32_t fn, int64_t n, int32_t d, int32_t k, int32_t t,
+                                    int32_t precision, int32_t max_iter) {
+  Prob pb{};
+  pb.n = n;
+  pb.d = d;
+  pb.ard = 1;
+  pb.D = d;
+  pb.p = d + 2;
+  pb.prec = precision;
+  if (n < 1 || d < 1 || d > kMaxD || t < 0 || k < 0 || max_iter < 0) return 0;
+  Arena A;
+  switch (fn) {
+    case GP_FN_KERNEL_MVM:
+    case GP_FN_KERNEL_GRAD_MVM: {
+      MvmPlan P;
+      plan_mvm(A, pb, std::max(t, 1), P);
+      if (fn == GP_FN_KERNEL_GRAD_MVM) {
+        PrepPlan pp;
+        (void)pp;
+        // the derivative products always run on CUDA cores
+        A.take<char>(elem_size(precision) * simt_scratch_elems(n, std::max(t, 1)));
+      }
+      break;
+    }
+    case GP_FN_PIVCHOL: {
+      PrepPlan pp;
+      plan_prep(A, pb, pp);
+      PivPlan P;
+      plan_piv(A, pb, k, P);
+      break;
+    }
+    case GP_FN_MBCG: {
+      MvmPlan mp;
+      plan_mvm(A, pb, std::max(t, 1), mp);
+      CorePlan cp;
+      plan_core(A, pb, k, cp);
+      if (precision == GP_FP64) {
+        CgBufs<double> c;
+        plan_cg<double>(A, pb, k, std::max(t, 1), std::max(max_iter, 1), c);
+      } else {
+        CgBufs<float> c;
+        plan_cg<float>(A, pb, k, std::max(t, 1), std::max(max_iter, 1), c);
+      }
+      break;
+    }
+    case GP_FN_MLL_AND_GRAD: {
+      int nl = std::max(t - 1, 0);
+      if (precision == GP_FP64) {
+        MllPlan<double> P;
+        plan_mll<double>(A, pb, k, nl, std::max(max_iter, 1), P);
+      } else {
+        MllPlan<float> P;
+        plan_mll<float>(A, pb, k, nl, std::max(max_iter, 1), P);
+      }
+      break;
+    }
+    default:
+      return 0;
+  }
+  return A.off + 256;
+}
+
+extern "C" const char* gp_status_string(int32_t s) {
+  switch (s) {
+    case GP_OK: return "GP_OK";
+    case GP_WARN_NOT_CONVERGED: return "GP_WARN_NOT_CONVERGED";
+    case GP_WARN_RANK_DEFICIENT: return "GP_WARN_RANK_DEFICIENT";
+    case GP_ERR_INVALID_ARG: return "GP_ERR_INVALID_ARG";
+    case GP_ERR_CUDA: return "GP_ERR_CUDA";
+    case GP_ERR_NOT_SPD: return "GP_ERR_NOT_SPD";
+    case GP_ERR_WORKSPACE: return "GP_ERR_WORKSPACE";
+    case GP_ERR_DEVICE_TIMEOUT: return "GP_ERR_DEVICE_TIMEOUT";
+    case GP_ERR_NUMERIC: return "GP_ERR_NUMERIC";
+    default: return "GP_UNKNOWN_STATUS";
+  }
+}
+
+extern "C" const char* gp_last_error_message(void) { return last_error(); }
+
+static gp_status check_ws(void* ws, size_t have, size_t need) {
+  if (have < need || (need > 256 && ws == nullptr)) {
+    set_error("workspace too small: need %zu bytes, got %zu", need, have);
+    return GP_ERR_WORKSPACE;
+  }
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    set_error("workspace must be 256-byte aligned");
+    return GP_ERR_WORKSPACE;
+  }
+  return GP_OK;
+}
+
+extern "C" gp_status gp_kernel_mvm(const gp_problem* prob, const void* V, int64_t ldv, int32_t t,
+                                   void* W, int64_t ldw, void* ws, size_t ws_bytes,
+                                   gp_stream_t stream) {
+  GP_TRY(check_problem(prob));
+  GP_REQUIRE(t >= 1 && t <= kMaxT, "t=%d out of range [1, %d]", t, kMaxT);
+  GP_REQUIRE(V && W, "V or W is NULL");
+  GP_REQUIRE(ldv >= prob->n && ldw >= prob->n, "leading dimensions must be >= n");
+  GP_REQUIRE(V != W, "W must not alias V");
+  Prob pb = make_prob(prob);
+  GP_TRY(check_ws(ws, ws_bytes, gp_workspace_size(GP_FN_KERNEL_MVM, pb.n, pb.d, 0, t, pb.prec, 1)));
+  GP_REQUIRE(!((pb.prec == GP_BF16 || pb.prec == GP_TF32) && !tc_supported(pb, t)),
+             "tensor-core precision does not support this shape");
+  Arena A;
+  A.base = static_cast<char*>(ws);
+  MvmPlan P;
+  plan_mvm(A, pb, t, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (pb.prec == GP_FP64) return run_kernel_mvm<double>(pb, V, ldv, t, W, ldw, P, st);
+  return run_kernel_mvm<float>(pb, V, ldv, t, W, ldw, P, st);
+}
+
+extern "C" gp_status gp_kernel_grad_mvm(const gp_problem* prob, const void* V, int64_t ldv,
+                                        int32_t t, void* dW, int64_t ldw, void* ws,
+                                        size_t ws_bytes, gp_stream_t stream) {
+  GP_TRY(check_problem(prob));
+  GP_REQUIRE(t >= 1 && t <= kMaxT, "t=%d out of range [1, %d]", t, kMaxT);
+  GP_REQUIRE(V && dW, "V or dW is NULL");
+  GP_REQUIRE(ldv >= prob->n && ldw >= prob->n, "leading dimensions must be >= n");
+  Prob pb = make_prob(prob);
+  GP_TRY(check_ws(ws, ws_bytes,
+                  gp_workspace_size(GP_FN_KERNEL_GRAD_MVM, pb.n, pb.d, 0, t, pb.prec, 1)));
+  Arena A;
+  A.base = static_cast<char*>(ws);
+  MvmPlan P;
+  plan_mvm(A, pb, t, P);
+  void* scratch = A.take<char>(elem_size(pb.prec) * simt_scratch_elems(pb.n, t));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (pb.prec == GP_FP64) {
+    GP_TRY(run_prep<double>(pb, P.prep, st));
+    return kdmvm_simt<double>(pb, P.prep.pr.Xs, V, ldv, t, dW, ldw, scratch, st);
+  }
+  GP_TRY(run_prep<float>(pb, P.prep, st));
+  return kdmvm_simt<float>(pb, P.prep.pr.Xs, V, ldv, t, dW, ldw, scratch, st);
+}
+
+extern "C" gp_status gp_pivchol(const gp_problem* prob, int32_t k, double tol,
+                                const int32_t* piv_override, void* L, int64_t ldl, int32_t* piv,
+                                int32_t* rank_out, void* ws, size_t ws_bytes,
+                                gp_stream_t stream) {
+  GP_TRY(check_problem(prob));
+  GP_REQUIRE(k >= 0 && k <= kMaxK && k <= prob->n, "k=%d out of range [0, min(n, %d)]", k,
+             kMaxK);
+  GP_REQUIRE(tol >= 0.0, "tol must be >= 0");
+  GP_REQUIRE(k == 0 || (L && piv), "L or piv is NULL");
+  GP_REQUIRE(rank_out, "rank_out is NULL");
+  GP_REQUIRE(ldl >= prob->n, "ldl must be >= n");
+  Prob pb = make_prob(prob);
+  GP_TRY(check_ws(ws, ws_bytes, gp_workspace_size(GP_FN_PIVCHOL, pb.n, pb.d, k, 1, pb.prec, 1)));
+  Arena A;
+  A.base = static_cast<char*>(ws);
+  PrepPlan pp;
+  plan_prep(A, pb, pp);
+  PivPlan P;
+  plan_piv(A, pb, k, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  GP_CUDA_TRY(cudaMemsetAsync(P.b.counter, 0, 4 * sizeof(unsigned), st));
+  if (pb.prec == GP_FP64) {
+    GP_TRY(run_prep<double>(pb, pp, st));
+    return pivchol_run<double>(pb, pp.pr.Xs, k, tol, piv_override, L, ldl, piv, rank_out, P.b, st);
+  }
+  GP_TRY(run_prep<float>(pb, pp, st));
+  return pivchol_run<float>(pb, pp.pr.Xs, k, tol, piv_override, L, ldl, piv, rank_out, P.b, st);
+}
+
+static gp_status check_opts(const gp_opts* o) {
+  GP_REQUIRE(o != nullptr, "opts is NULL");
+  GP_REQUIRE(o->max_iter >= 1 && o->max_iter <= 8192, "max_iter=%d out of range [1, 8192]",
+             o->max_iter);
+  GP_REQUIRE(o->cg_tol >= 0.0, "cg_tol must be >= 0");
+  GP_REQUIRE(o->recompute_every >= 0, "recompute_every must be >= 0");
+  GP_REQUIRE(o->pivchol_tol >= 0.0, "pivchol_tol must be >= 0");
+  return GP_OK;
+}
+
+namespace gp {
+namespace {
+template <class T>
+gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, int64_t ldb,
+                    int t, const int* iters_override, T* Xsol, int64_t ldx, T* PinvB,
+                    double* T_diag, double* T_off, double* rho0, int* iters, int* status,
+                    const gp_opts& o, void* ws, size_t ws_bytes, cudaStream_t st) {
+  Arena A;
+  A.base = static_cast<char*>(ws);
+  MvmPlan mp;
+  plan_mvm(A, pb, t, mp);
+  CorePlan cp;
+  plan_core(A, pb, k, cp);
+  CgBufs<T> cb;
+  plan_cg<T>(A, pb, k, t, o.max_iter, cb);
+  (void)ws_bytes;
+  GP_CUDA_TRY(cudaMemsetAsync(cb.counter, 0, 4 * sizeof(unsigned), st));
+  GP_CUDA_TRY(cudaMemsetAsync(cb.status, 0, sizeof(int), st));
+  GP_CUDA_TRY(cudaMemsetAsync(cb.alpha, 0, sizeof(double) * (size_t)t * o.max_iter, st));
+  GP_CUDA_TRY(cudaMemsetAsync(cb.beta, 0, sizeof(double) * (size_t)t * o.max_iter, st));
+  GP_TRY(run_prep<T>(pb, mp.prep, st));
+  if (k > 0) GP_TRY(atb<T>(pb.n, L, ldl, k, L, ldl, k, cp.atb_part, cp.G, st));
+  GP_TRY(woodbury_core(k, cp.G, pb.theta, pb.D, pb.n, cp.Cfac, cp.Cinv, cp.work, cp.logdet,
+                       cb.status, st));
+  int host_status = 0;
+  if (mp.use_tc) {
+    GP_TRY(tc_prepare_inputs(pb, mp.prep.pr.Xs, mp.tc, st));
+    TcMvm op;
+    op.pb = pb;
+    op.tb = mp.tc;
+    GP_TRY(cg_solve<T>(pb, op, L, ldl, k, cp.Cinv, B, ldb, t, iters_override, o, cb, PinvB, ldx,
+                       &host_status, st));
+  } else {
+    SimtMvm<T> op;
+    op.pb = pb;
+    op.Xs = mp.prep.pr.Xs;
+    op.scratch = mp.scratch;
+    GP_TRY(cg_solve<T>(pb, op, L, ldl, k, cp.Cinv, B, ldb, t, iters_override, o, cb, PinvB, ldx,
+                       &host_status, st));
+  }
+  // outputs
+  GP_CUDA_TRY(cudaMemcpy2DAsync(Xsol, sizeof(T) * ldx, cb.X, sizeof(T) * pb.n, sizeof(T) * pb.n,
+                                t, cudaMemcpyDeviceToDevice, st));
+  GP_TRY(cg_tridiag<T>(t, o.max_iter, cb, T_diag, T_off, st));
+  GP_CUDA_TRY(cudaMemcpyAsync(rho0, cb.rho0, sizeof(double) * t, cudaMemcpyDeviceToDevice, st));
+  GP_CUDA_TRY(cudaMemcpyAsync(iters, cb.iters, sizeof(int) * t, cudaMemcpyDeviceToDevice, st));
+  GP_CUDA_TRY(cudaMemcpyAsync(status, cb.status, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  int hs = 0;
+  GP_CUDA_TRY(cudaMemcpyAsync(&hs, cb.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hs < 0) return (gp_status)hs;
+  return GP_OK;
+}
+}  // namespace
+}  // namespace gp
+
+extern "C" gp_status gp_mbcg(const gp_problem* prob, const void* L, int64_t ldl, int32_t k,
+                             const void* B, int64_t ldb, int32_t t,
+                             const int32_t* iters_override, void* Xsol, int64_t ldx, void* PinvB,
+                             double* T_diag, double* T_off, double* rho0, int32_t* iters,
+                             int32_t* status, const gp_opts* opts, void* ws, size_t ws_bytes,
+                             gp_stream_t stream) {
+  GP_TRY(check_problem(prob));
+  GP_TRY(check_opts(opts));
+  GP_REQUIRE(t >= 1 && t <= kMaxT, "t=%d out of range [1, %d]", t, kMaxT);
+  GP_REQUIRE(k >= 0 && k <= kMaxK && k <= prob->n, "k out of range");
+  GP_REQUIRE(k == 0 || L, "L is NULL");
+  GP_REQUIRE(B && Xsol && T_diag && T_off && rho0 && iters && status, "NULL output");
+  GP_REQUIRE(ldl >= prob->n && ldb >= prob->n && ldx >= prob->n, "leading dimensions must be >= n");
+  Prob pb = make_prob(prob);
+  GP_REQUIRE(!((pb.prec == GP_BF16 || pb.prec == GP_TF32) && !tc_supported(pb, t)),
+             "tensor-core precision does not support this shape");
+  GP_TRY(check_ws(ws, ws_bytes,
+                  gp_workspace_size(GP_FN_MBCG, pb.n, pb.d, k, t, pb.prec, opts->max_iter)));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (pb.prec == GP_FP64)
+    return mbcg_impl<double>(pb, (const double*)L, ldl, k, (const double*)B, ldb, t,
+                             iters_override, (double*)Xsol, ldx, (double*)PinvB, T_diag, T_off,
+                             rho0, iters, status, *opts, ws, ws_bytes, st);
+  return mbcg_impl<float>(pb, (const float*)L, ldl, k, (const float*)B, ldb, t, iters_override,
+                          (float*)Xsol, ldx, (float*)PinvB, T_diag, T_off, rho0, iters, status,
+                          *opts, ws, ws_bytes, st);
+}
+
+extern "C" gp_status gp_mll_and_grad(const gp_problem* prob, const void* y, int32_t k,
+                                     int32_t n_probes, const int8_t* eps_override,
+                                     const int32_t* piv_override, const int32_t* iters_override,
+                                     double* out, int32_t* iout, const gp_opts* opts, void* ws,
+                                     size_t ws_bytes, gp_stream_t stream) {
+  GP_TRY(check_problem(prob));
+  GP_TRY(check_opts(opts));
+  GP_REQUIRE(y && out && iout, "y, out or iout is NULL");
+  GP_REQUIRE(k >= 0 && k <= kMaxK && k <= prob->n, "k=%d out of range [0, min(n, %d)]", k, kMaxK);
+  GP_REQUIRE(n_probes >= 0 && n_probes + 1 <= kMaxT, "n_probes=%d out of range", n_probes);
+  Prob pb = make_prob(prob);
+  const int t = n_probes + 1;
+  GP_REQUIRE(!((pb.prec == GP_BF16 || pb.prec == GP_TF32) && !tc_supported(pb, t)),
+             "tensor-core precision does not support this shape");
+  GP_TRY(check_ws(ws, ws_bytes,
+                  gp_workspace_size(GP_FN_MLL_AND_GRAD, pb.n, pb.d, k, t, pb.prec, opts->max_iter)));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (pb.prec == GP_FP64)
+    return mll_impl<double>(pb, (const double*)y, k, n_probes, eps_override, piv_override,
+                            iters_override, out, iout, *opts, ws, ws_bytes, st);
+  return mll_impl<float>(pb, (const float*)y, k, n_probes, eps_override, piv_override,
+                         iters_override, out, iout, *opts, ws, ws_bytes, st);
+}
+
+extern "C" gp_status gp_rademacher(uint64_t seed, int32_t stream_id, int64_t rows, int32_t cols,
+                                   int8_t* out, gp_stream_t stream) {
+  GP_REQUIRE(rows >= 0 && cols >= 0, "negative size");
+  GP_REQUIRE(rows * cols == 0 || out, "out is NULL");
+  GP_REQUIRE(stream_id == 1 || stream_id == 2, "stream_id must be 1 or 2");
+  return rademacher_fill(seed, stream_id, rows, cols, out, reinterpret_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,319 @@
+"""CUDA path vs the FP64 oracle, element by element on the same seeded inputs.
+
+Every call goes through the C ABI (paper_2107_00243_gb300.gp).  Sizes span several
+128-row tiles and a ragged tail.  Tolerances:
+  FP64 mode    1e-10 relative (rounding order only)
+  FP32 mode    1e-4 relative per estimator result (log-det, quadratic term, MLL,
+               each gradient entry against 1/2(|quad_p| + |trace_p|)); kernel
+               products 2e-5 normwise
+Integer work (probe signs, pivots, iteration counts) is compared exactly, except
+that a pivot may differ from the oracle's where the oracle's own residual
+diagonal has a near tie (both picks are then valid greedy choices).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import estimator, kernels, lanczos, mbcg as omb, pivchol, probes, woodbury
+from paper_2107_00243_gb300 import gp, workloads
+
+pytestmark = pytest.mark.gpu
+
+KTOL = {gp.FP64: 1e-11, gp.FP32: 2e-5}
+ETOL = {gp.FP64: 1e-9, gp.FP32: 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2107_00243_gb300 import build
+    build.build()
+    gp.load()
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _problem(n, d, kind, ard, seed=0, lo=0.3, hi=1.0, s2=0.05):
+    return workloads.random_problem(n, d, kind=kind, ard=ard, seed=seed, lo=lo, hi=hi, s2=s2)
+
+
+# ---------------------------------------------------------------------------- probes
+@pytest.mark.parametrize("seed", [0, 7, 2 ** 63 + 5])
+@pytest.mark.parametrize("stream", [1, 2])
+def test_rademacher_bit_exact(seed, stream):
+    got = gp.gp_rademacher(seed, stream, 1337, 33).cpu().numpy().astype(np.float64)
+    ref = probes.rademacher(seed, stream, 1337, 33)
+    np.testing.assert_array_equal(got, ref)
+
+
+# ------------------------------------------------------------------- kernel products
+SHAPES = [(1000, 3, 11), (777, 16, 33), (130, 1, 1), (1, 2, 3), (300, 20, 70), (257, 5, 64)]
+
+
+@pytest.mark.parametrize("prec", [gp.FP64, gp.FP32])
+@pytest.mark.parametrize("kind", kernels.KINDS)
+@pytest.mark.parametrize("ard", [True, False])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_kernel_mvm(prec, kind, ard, shape):
+    n, d, t = shape
+    p = _problem(n, d, kind, ard, seed=n + d)
+    V = np.random.default_rng(1).standard_normal((n, t))
+    op = kernels.KernelOperator(kind, p.X, p.theta, ard)
+    ref = op.matvec(V)
+    prob = gp.Problem(p.X, p.theta, kind, ard, prec)
+    got = gp.gp_kernel_mvm(prob, torch.from_numpy(V)).cpu().numpy()
+    assert _rel(got, ref) <= KTOL[prec], _rel(got, ref)
+
+
+@pytest.mark.parametrize("prec", [gp.FP64, gp.FP32])
+@pytest.mark.parametrize("kind", kernels.KINDS)
+@pytest.mark.parametrize("ard", [True, False])
+def test_kernel_grad_mvm(prec, kind, ard):
+    n, d, t = 433, 4, 7
+    p = _problem(n, d, kind, ard, seed=3)
+    V = np.random.default_rng(2).standard_normal((n, t))
+    op = kernels.KernelOperator(kind, p.X, p.theta, ard)
+    refs = op.grad_matvec(V)
+    prob = gp.Problem(p.X, p.theta, kind, ard, prec)
+    got = gp.gp_kernel_grad_mvm(prob, torch.from_numpy(V)).cpu().numpy()
+    assert got.shape == (prob.p, n, t)
+    for q in range(prob.p):
+        assert _rel(got[q], refs[q]) <= KTOL[prec], (q, _rel(got[q], refs[q]))
+
+
+# -------------------------------------------------------------------- pivoted Cholesky
+def _check_pivots_valid(piv_gpu, op, L_ref, piv_ref, rel_tie=1e-4):
+    """Pivots equal the oracle's; where they first differ, the GPU pick must be a
+    near-tie of the oracle's residual diagonal at that step."""
+    d0 = op.diag()
+    for m in range(len(piv_ref)):
+        if piv_gpu[m] == piv_ref[m]:
+            continue
+        dres = d0 - np.sum(L_ref[:, :m] ** 2, axis=1)
+        dres[piv_ref[:m]] = -np.inf
+        assert dres[piv_gpu[m]] >= dres.max() * (1 - rel_tie), (m, piv_gpu[m], piv_ref[m])
+        return m
+    return len(piv_ref)
+
+
+@pytest.mark.parametrize("prec", [gp.FP64, gp.FP32])
+@pytest.mark.parametrize("kind", kernels.KINDS)
+def test_pivchol(prec, kind):
+    n, d, k = 1100, 3, 40
+    p = _problem(n, d, kind, True, seed=5)
+    op = kernels.KernelOperator(kind, p.X, p.theta, True)
+    L_ref, piv_ref, rank_ref, _ = pivchol.pivoted_cholesky(op, k)
+    prob = gp.Problem(p.X, p.theta, kind, True, prec)
+    L, piv, rank = gp.gp_pivchol(prob, k)
+    L, piv, rank = L.cpu().numpy(), piv.cpu().numpy(), int(rank.item())
+    assert rank == rank_ref == k
+    agree = _check_pivots_valid(piv, op, L_ref, piv_ref)
+    if agree == k:
+        assert _rel(L, L_ref) <= (1e-9 if prec == gp.FP64 else 2e-4)
+    # matched: the oracle's pivot order forced on the GPU
+    Lm, pivm, rankm = gp.gp_pivchol(prob, k, piv_override=piv_ref)
+    np.testing.assert_array_equal(pivm.cpu().numpy(), piv_ref)
+    assert _rel(Lm.cpu().numpy(), L_ref) <= (1e-9 if prec == gp.FP64 else 2e-4)
+
+
+def test_pivchol_rank_deficient_and_tolerance():
+    rng = np.random.default_rng(9)
+    base = rng.uniform(size=(6, 2))
+    X = np.repeat(base, 5, axis=0)                 # 30 points, 6 distinct
+    theta = np.array([0.5, 0.5, 1.0, 0.01])
+    op = kernels.KernelOperator(kernels.RBF, X, theta, True)
+    _, piv_ref, rank_ref, _ = pivchol.pivoted_cholesky(op, 20)
+    prob = gp.Problem(X, theta, kernels.RBF, True, gp.FP64)
+    L, piv, rank = gp.gp_pivchol(prob, 20)
+    assert int(rank.item()) == rank_ref <= 6
+    np.testing.assert_array_equal(piv.cpu().numpy()[:rank_ref], piv_ref)
+    assert np.all(piv.cpu().numpy()[rank_ref:] == -1)
+    assert np.all(L.cpu().numpy()[:, rank_ref:] == 0)
+    # residual-trace tolerance
+    p = _problem(500, 1, kernels.RBF, True, seed=4, lo=0.3, hi=0.3)
+    op = kernels.KernelOperator(p.kind, p.X, p.theta, True)
+    _, piv_t, rank_t, _ = pivchol.pivoted_cholesky(op, 100, tol=1e-6)
+    prob = gp.Problem(p.X, p.theta, p.kind, True, gp.FP64)
+    _, piv_g, rank_g = gp.gp_pivchol(prob, 100, tol=1e-6)
+    assert int(rank_g.item()) == rank_t < 100
+    np.testing.assert_array_equal(piv_g.cpu().numpy()[:rank_t], piv_t)
+
+
+# ---------------------------------------------------------------------------- mBCG
+@pytest.mark.parametrize("prec", [gp.FP64, gp.FP32])
+@pytest.mark.parametrize("k", [0, 12])
+def test_mbcg_matched(prec, k):
+    n, t = 900, 5
+    p = _problem(n, 2, kernels.MATERN32, True, seed=6, s2=0.02)
+    op = kernels.KernelOperator(p.kind, p.X, p.theta, True)
+    L, piv, rank, _ = pivchol.pivoted_cholesky(op, k)
+    B = np.random.default_rng(3).standard_normal((n, t))
+    B[:, 2] *= 1e-3
+    tol, max_iter = 1e-6, 300
+    ref = omb.mbcg(op.matvec, lambda V: woodbury.solve(L, op.s2, V), B, tol, max_iter, 7)
+    prob = gp.Problem(p.X, p.theta, p.kind, True, prec)
+    o = gp.opts(cg_tol=tol, max_iter=max_iter, recompute_every=7)
+    res = gp.gp_mbcg(prob, torch.from_numpy(L) if k else None, torch.from_numpy(B), o,
+                     iters_override=ref["iters"])
+    np.testing.assert_array_equal(res["iters"].cpu().numpy(), ref["iters"])
+    tol_x = 1e-9 if prec == gp.FP64 else 2e-4
+    assert _rel(res["X"].cpu().numpy(), ref["X"]) <= tol_x
+    assert _rel(res["PinvB"].cpu().numpy(), ref["z0"]) <= (1e-12 if prec == gp.FP64 else 1e-5)
+    assert _rel(res["rho0"].cpu().numpy(), ref["rho0"]) <= (1e-12 if prec == gp.FP64 else 1e-5)
+    Td, To = res["T_diag"].cpu().numpy(), res["T_off"].cpu().numpy()
+    for c in range(t):
+        m = int(ref["iters"][c])
+        dg, of = lanczos.tridiag_from_cg(ref["alpha"][c], ref["beta"][c], m)
+        assert _rel(Td[c, :m], dg) <= (1e-9 if prec == gp.FP64 else 1e-3)
+        if m > 1:
+            assert _rel(To[c, :m - 1], of) <= (1e-9 if prec == gp.FP64 else 1e-3)
+    # unmatched: the GPU's own stopping decisions
+    res2 = gp.gp_mbcg(prob, torch.from_numpy(L) if k else None, torch.from_numpy(B), o)
+    assert np.all(np.abs(res2["iters"].cpu().numpy() - ref["iters"]) <= 2)
+
+
+# ------------------------------------------------------------------ full estimator
+def _compare(r, ref, tol):
+    errs = {
+        "mll": abs(r["mll"] - ref["mll"]) / abs(ref["mll"]),
+        "quad": abs(r["quad"] - ref["quad"]) / abs(ref["quad"]),
+        "logdet": abs(r["logdet"] - ref["logdet"]) / abs(ref["logdet"]),
+        "logdetP": abs(r["logdetP"] - ref["logdetP"]) / abs(ref["logdetP"]),
+    }
+    scale = 0.5 * (np.abs(ref["quad_p"]) + np.abs(ref["trace_p"]))
+    g = np.abs(r["grad"] - ref["grad"]) / np.maximum(scale, 1e-300)
+    for q in range(len(g)):
+        errs[f"grad{q}"] = g[q]
+    errs["trP"] = _rel(r["trP_p"], ref["trP_p"])
+    errs["probeP"] = np.max(np.abs(r["probeP_p"] - ref["probeP_p"]) /
+                            np.maximum(scale, 1e-300))
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (bad, errs)
+    return errs
+
+
+def _run_matched(p, prec, tol_override=None):
+    ref = estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, p.k, p.n_probes, p.tol,
+                                 p.max_iter, seed=p.seed, recompute_every=p.recompute_every)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, prec)
+    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, recompute_every=p.recompute_every,
+                seed=p.seed)
+    st, out, iout = gp.gp_mll_and_grad(prob, p.y, p.k, p.n_probes, o, piv_override=ref["piv"],
+                                       iters_override=ref["iters"])
+    r = gp.unpack(out, iout, prob.p, p.n_probes, p.k)
+    assert st >= 0 and r["status"] == 0
+    np.testing.assert_array_equal(r["iters"], ref["iters"])
+    np.testing.assert_array_equal(r["piv"], ref["piv"])
+    return r, ref, _compare(r, ref, tol_override or ETOL[prec])
+
+
+def test_estimator_small_rbf_fp64_full_size():
+    """The small RBF workload (n=1,000, d=3, k=20, l=10, tol 1e-6, FP64)."""
+    _run_matched(workloads.c1_small_rbf(), gp.FP64)
+
+
+@pytest.mark.parametrize("kind", kernels.KINDS)
+@pytest.mark.parametrize("ard", [True, False])
+def test_estimator_kinds_fp64(kind, ard):
+    p = workloads.random_problem(611, 3, kind=kind, ard=ard, seed=21, s2=0.03, k=15,
+                                 n_probes=6, tol=1e-8, max_iter=300)
+    p.recompute_every = 10
+    _run_matched(p, gp.FP64)
+
+
+def test_estimator_matern52_ard_fp32():
+    """The Matern-5/2 ARD workload (d=8, k=100, l=50, tol 1e-3) on a 2,500-point subsample."""
+    p = workloads.subsample(workloads.c2_matern52_ard(n=20000), 2500)
+    _run_matched(p, gp.FP32)
+
+
+def test_estimator_rbf_ard_fp32_small_c3_shape():
+    """RBF ARD d=16 (the n=1e5 workload's shape) on a 3,000-point subsample, FP32."""
+    p = workloads.subsample(workloads.c3_rbf_ard_1e5(n=20000, precision=gp.FP32), 3000)
+    _run_matched(p, gp.FP32)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_estimator_edge_ranks(k):
+    p = workloads.random_problem(257, 2, seed=22, k=k, n_probes=3, tol=1e-9, max_iter=257)
+    _run_matched(p, gp.FP64)
+
+
+def test_estimator_single_probe_and_tiny_n():
+    p = workloads.random_problem(5, 1, seed=23, k=2, n_probes=1, tol=1e-12, max_iter=5)
+    _run_matched(p, gp.FP64, tol_override=1e-8)
+
+
+def test_estimator_unmatched_and_statistical():
+    """GPU's own pivots and stopping; checked against the exact FP64 values within the
+    statistical bound (4 standard errors of the l per-probe terms) plus the CG term."""
+    from oracle import exact
+    p = workloads.random_problem(700, 2, kind=kernels.MATERN32, seed=24, s2=0.05, k=20,
+                                 n_probes=64, tol=1e-8, max_iter=700)
+    ex = exact.exact_mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, gp.FP32)
+    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, seed=11)
+    st, out, iout = gp.gp_mll_and_grad(prob, p.y, p.k, p.n_probes, o)
+    r = gp.unpack(out, iout, prob.p, p.n_probes, p.k)
+    se = np.std(r["gamma"], ddof=1) / np.sqrt(p.n_probes)
+    assert abs(r["logdet"] - ex["logdet"]) <= 4 * se + 1e-3
+    assert abs(r["quad"] - ex["quad"]) <= 1e-4 * abs(ex["quad"])
+
+
+def test_eps_override_matches_generator():
+    p = workloads.random_problem(300, 2, seed=25, k=8, n_probes=4, tol=1e-9, max_iter=300)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, gp.FP64)
+    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, seed=123)
+    e1, e2 = probes.eps_pair(123, p.k, p.n, p.n_probes)
+    eps = np.concatenate([e1, e2], axis=0)              # (k + n, l)
+    _, out1, iout1 = gp.gp_mll_and_grad(prob, p.y, p.k, p.n_probes, o)
+    out1 = out1.clone()
+    _, out2, iout2 = gp.gp_mll_and_grad(prob, p.y, p.k, p.n_probes, o,
+                                        eps_override=torch.from_numpy(eps))
+    np.testing.assert_array_equal(out1.cpu().numpy(), out2.cpu().numpy())
+
+
+# ---------------------------------------------------------------- full-size samples
+def test_kernel_mvm_full_size_sampled_rows():
+    """n=1e5, d=16, t=33 (the large RBF ARD workload): 64 sampled rows of K_hat V
+    against the oracle, computed row by row."""
+    p = workloads.c3_rbf_ard_1e5(precision=gp.FP32)
+    V = np.random.default_rng(5).standard_normal((p.n, 33))
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, gp.FP32)
+    got = gp.gp_kernel_mvm(prob, torch.from_numpy(V)).cpu().numpy()
+    rows = np.random.default_rng(6).choice(p.n, 64, replace=False)
+    Kr = kernels.kernel_block(p.kind, p.X[rows], p.X, p.theta, p.ard)
+    ref = Kr @ V + p.theta[-1] * V[rows]
+    scale = (np.abs(Kr) @ np.abs(V)).max()
+    assert np.abs(got[rows] - ref).max() <= 1e-5 * scale
+
+
+def test_pivchol_full_size_prefix():
+    """n=1e5, d=16: the first 12 pivots and columns of the rank-200 factor."""
+    p = workloads.c3_rbf_ard_1e5(precision=gp.FP32)
+    op = kernels.KernelOperator(p.kind, p.X, p.theta, p.ard)
+    L_ref, piv_ref, _, _ = pivchol.pivoted_cholesky(op, 12)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, gp.FP32)
+    L, piv, rank = gp.gp_pivchol(prob, 200)
+    assert int(rank.item()) == 200
+    piv = piv.cpu().numpy()
+    m = _check_pivots_valid(piv[:12], op, L_ref, piv_ref)
+    assert _rel(L[:, :m].cpu().numpy(), L_ref[:, :m]) <= 1e-4
+
+
+def test_estimator_full_size_properties():
+    """The whole estimator at n=1e5 (FP32): finite outputs, full rank k with distinct
+    pivots, every column stopped by the tolerance, y^T K^-1 y > 0."""
+    p = workloads.c3_rbf_ard_1e5(precision=gp.FP32)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, gp.FP32)
+    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, recompute_every=p.recompute_every, seed=0)
+    st, out, iout = gp.gp_mll_and_grad(prob, p.y, p.k, p.n_probes, o)
+    r = gp.unpack(out, iout, prob.p, p.n_probes, p.k)
+    assert st == 0 and r["rank"] == p.k
+    assert np.all(np.isfinite(out.cpu().numpy()))
+    assert np.all(r["iters"] >= 1) and np.all(r["iters"] < p.max_iter)
+    assert len(set(r["piv"].tolist())) == p.k
+    assert r["quad"] > 0
