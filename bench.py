@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Seconds per MLL + gradient evaluation of the preconditioned GP estimator.
+
+Workload (synthetic stand-in for the paper's UCI regressions, Sec. 5): n = 100,000
+points uniform on [0,1]^16, targets a sum of 16 random sinusoids plus noise, RBF
+ARD kernel with lengthscales in [0.2, 1], s = 1, sigma^2 = 0.01; pivoted-Cholesky
+preconditioner of rank k = 200, l = 32 probes, CG tolerance 1e-2, true residual
+every 25 steps.  One step = one call of gp_mll_and_grad (Alg. 1 + Alg. 2: pivoted
+Cholesky, Woodbury core, probes, mBCG, Lanczos quadrature, gradient contraction,
+preconditioner terms) on inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision bf16|tf32|fp32]
+
+Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own replica
+(the estimator does not shard; the metric is whole-job seconds per evaluation).
+``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s per MLL+grad eval at N=1e5 (mixed vs FP32 GPU); kernel-MVM TFLOP/s vs peak"
+WORKLOAD = "rbf_ard_n100000_d16_k200_l32_tol1e-2"
+SAMPLE_N = 2000          # oracle sample: a 2,000-point subsample of the same workload
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _traffic_from_profiles(kernel_tag):
+    """Per-launch DRAM bytes recorded from an ncu capture (profiles/*traffic*.txt)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 2 and parts[0] == kernel_tag:
+                try:
+                    return float(parts[1])
+                except ValueError:
+                    return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def _max_over_ranks(value, dist):
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def oracle_sample_seconds(reps=3):
+    """The FP64 oracle, as it stands, on a 2,000-point subsample of the workload:
+    median seconds over `reps` evaluations and the thread count it used."""
+    import numpy as np
+    from oracle import estimator
+    from paper_2107_00243_gb300 import workloads
+    p = workloads.subsample(workloads.c3_rbf_ard_1e5(), SAMPLE_N)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, p.k, p.n_probes, p.tol,
+                               p.max_iter, recompute_every=p.recompute_every)
+        times.append(time.perf_counter() - t0)
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return statistics.median(times), times, cores
+
+
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        _barrier(dist)
+        return
+    scale = (100000 / SAMPLE_N) ** 2
+    per_step = []
+    cores = os.cpu_count() or 1
+    for i in range(args.warmup + args.steps):
+        med, _, cores = oracle_sample_seconds(reps=1)
+        if i >= args.warmup:
+            per_step.append(med * scale)
+    value = statistics.mean(per_step)
+    sample = (f"FP64 oracle (numpy) full estimator on a {SAMPLE_N}-point subsample of the "
+              f"n=1e5 workload, scaled by (1e5/{SAMPLE_N})^2 (its O(n^2) kernel products "
+              "dominate)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64-cpu-oracle"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    _barrier(dist)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["bf16", "tf32", "fp32"], default="fp32")
+    ap.add_argument("--fp32-steps", type=int, default=2,
+                    help="timed steps of the plain FP32 form when --precision is mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, ws, local, dist = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank, ws, dist)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+    from paper_2107_00243_gb300 import build, gp, workloads
+    build.build()
+    gp.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prec = {"bf16": gp.BF16, "tf32": gp.TF32, "fp32": gp.FP32}[args.precision]
+
+    p = workloads.c3_rbf_ard_1e5(precision=prec)
+    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, recompute_every=p.recompute_every,
+                seed=p.seed)
+    t = p.n_probes + 1
+
+    def setup(precision):
+        prob = gp.Problem(p.X, p.theta, p.kind, p.ard, precision, device=dev)
+        wsp = gp.Workspace()
+        out = torch.empty(gp.out_len(prob.p, p.n_probes), dtype=torch.float64, device=dev)
+        iout = torch.empty(2 + t + p.k, dtype=torch.int32, device=dev)
+        y = torch.as_tensor(p.y).to(device=dev, dtype=prob.dtype)
+        return prob, wsp, out, iout, y
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def timed_steps(prob, wsp, out, iout, y, steps, measure_mvm=False):
+        stream = torch.cuda.current_stream()
+        total = 0.0
+        gp.mvm_timing(measure_mvm)
+        gp.mvm_timing_read()
+        l0 = gp.launch_count()
+        for _ in range(steps):
+            flush.fill_(1)                                     # L2 flush between steps
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gp.gp_mll_and_grad(prob, y, p.k, p.n_probes, o, workspace=wsp, out=out, iout=iout)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1) / 1e3
+        launches = gp.launch_count() - l0
+        mvm_ms, mvm_n = gp.mvm_timing_read()
+        gp.mvm_timing(False)
+        return total, launches, mvm_ms, mvm_n
+
+    prob, wsp, out, iout, y = setup(prec)
+    for _ in range(args.warmup):
+        gp.gp_mll_and_grad(prob, y, p.k, p.n_probes, o, workspace=wsp, out=out, iout=iout)
+    torch.cuda.synchronize()
+    res = gp.unpack(out, iout, prob.p, p.n_probes, p.k)
+
+    sampler = ClockSampler(local)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    sampler.start()
+    total, launches, mvm_ms, mvm_n = timed_steps(prob, wsp, out, iout, y, args.steps,
+                                                 measure_mvm=True)
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    _barrier(dist)
+    total = _max_over_ranks(total, dist)
+    value = total / (args.steps * ws)
+
+    # the plain FP32 form of the same evaluation (speedup denominator of the mixed path)
+    fp32_value = None
+    if prec != gp.FP32 and args.fp32_steps > 0:
+        prob32, wsp32, out32, iout32, y32 = setup(gp.FP32)
+        for _ in range(3):
+            gp.gp_mll_and_grad(prob32, y32, p.k, p.n_probes, o, workspace=wsp32, out=out32,
+                               iout=iout32)
+        tot32, _, _, _ = timed_steps(prob32, wsp32, out32, iout32, y32, args.fp32_steps)
+        fp32_value = _max_over_ranks(tot32, dist) / (args.fp32_steps * ws)
+        del wsp32, out32, iout32
+
+    # end to end: host (pinned) inputs -> device -> estimator -> host outputs
+    Xh = torch.as_tensor(p.X).to(prob.dtype).pin_memory()
+    yh = torch.as_tensor(p.y).to(prob.dtype).pin_memory()
+    th = torch.as_tensor(p.theta).to(torch.float64).pin_memory()
+    outh = torch.empty(out.numel(), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    stream = torch.cuda.current_stream()
+    e2e_total = 0.0
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prob.X.copy_(Xh, non_blocking=True)
+        y.copy_(yh, non_blocking=True)
+        prob.theta.copy_(th, non_blocking=True)
+        gp.gp_mll_and_grad(prob, y, p.k, p.n_probes, o, workspace=wsp, out=out, iout=iout)
+        outh.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_total += e0.elapsed_time(e1) / 1e3
+    e2e_total = _max_over_ranks(e2e_total, dist)
+    e2e_value = e2e_total / (e2e_steps * ws)
+    h2d = Xh.numel() * Xh.element_size() + yh.numel() * yh.element_size() + th.numel() * 8
+    d2h = outh.numel() * 8
+
+    if rank != 0:
+        return
+
+    # roofline of the dominant kernel: the kernel-matrix product (algorithmic FLOPs
+    # 2 n^2 (d + t) per product; d = 16, t = 33)
+    peaks, peak_src = _peaks()
+    flops_per = 2.0 * p.n * p.n * (p.d + t)
+    avg_mvm_s = (mvm_ms / 1e3) / max(mvm_n, 1)
+    achieved = flops_per / avg_mvm_s / 1e12 if mvm_n else None
+    if prec == gp.FP32:
+        bound = "alu"
+        peak = SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak_note = ("FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock "
+                     f"({peaks.get('sm_max_mhz', 2070.0):.0f} MHz, {peak_src})")
+    else:
+        bound = "tensor"
+        bf = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = bf if prec == gp.BF16 else bf / 2.0
+        peak_note = (f"bf16 dense sustained, {peak_src}" if prec == gp.BF16 else
+                     f"tf32 = bf16 sustained ({peak_src}) x 1/2 (nominal ratio)")
+    kernel_tag = {gp.FP32: "kmvm_simt_fp32", gp.BF16: "kmvm_tc_bf16",
+                  gp.TF32: "kmvm_tc_tf32"}[prec]
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": _traffic_from_profiles(kernel_tag), "kernel": kernel_tag,
+            "peak_source": peak_note, "algorithmic_flops_per_product": flops_per,
+            "products_timed": mvm_n, "avg_product_ms": avg_mvm_s * 1e3}
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        med, times, cores = oracle_sample_seconds(reps=3)
+        scale = (100000 / SAMPLE_N) ** 2
+        cpu = {"value": med * scale, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": (f"FP64 oracle full estimator on a {SAMPLE_N}-point subsample of the "
+                          f"same workload, median of 3 ({', '.join(f'{x:.2f}' for x in times)} s),"
+                          f" scaled by (1e5/{SAMPLE_N})^2")}
+
+    dtype = {gp.FP32: "f32", gp.BF16: "bf16", gp.TF32: "tf32"}[prec]
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": value * 1e3 * ws, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "n": p.n, "d": p.d,
+                   "k": p.k, "n_probes": p.n_probes, "cg_tol": p.tol,
+                   "recompute_every": p.recompute_every, "l2": "flushed between steps",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "fp32_form_s_per_eval": fp32_value,
+        "speedup_vs_fp32_form": (fp32_value / value) if fp32_value else None,
+        "iters": res["iters"].tolist(), "mll": res["mll"], "status": res["status"],
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches / max(args.steps, 1),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

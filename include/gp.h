@@ -196,6 +196,15 @@ const char* gp_status_string(int32_t status);
 /* Detail of the last host-side validation failure on this thread (static storage). */
 const char* gp_last_error_message(void);
 
+/* Instrumentation.  gp_launch_count: kernels this library has launched since it
+ * was loaded (host-side count of launch sites).  gp_mvm_timing(1) makes the CG
+ * loop of gp_mbcg / gp_mll_and_grad bracket every kernel-matrix product with CUDA
+ * events on the caller's stream; gp_mvm_timing_read returns (and resets) their
+ * summed duration in ms and the number of products timed.                        */
+int64_t gp_launch_count(void);
+void gp_mvm_timing(int32_t enable);
+gp_status gp_mvm_timing_read(double* total_ms, int64_t* products);
+
 /* Rademacher signs of the probe generator, for inspection:
  * out[c * rows + r] = +-1 for stream 1 (eps1) or 2 (eps2).  Asynchronous.         */
 gp_status gp_rademacher(uint64_t seed, int32_t stream_id, int64_t rows, int32_t cols,

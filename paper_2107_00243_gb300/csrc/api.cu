@@ -655,3 +655,69 @@ extern "C" gp_status gp_rademacher(uint64_t seed, int32_t stream_id, int64_t row
   GP_REQUIRE(stream_id == 1 || stream_id == 2, "stream_id must be 1 or 2");
   return rademacher_fill(seed, stream_id, rows, cols, out, reinterpret_cast<cudaStream_t>(stream));
 }
+
+// ---- instrumentation ---------------------------------------------------------------------
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+namespace gp {
+namespace {
+std::atomic<long long> g_launches{0};
+std::atomic<int> g_timing{0};
+std::mutex g_tmu;
+std::vector<cudaEvent_t> g_free_events;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_pairs;
+cudaEvent_t g_open = nullptr;
+cudaEvent_t take_event() {
+  if (!g_free_events.empty()) {
+    cudaEvent_t e = g_free_events.back();
+    g_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool mvm_timing_enabled() { return g_timing.load() != 0; }
+void mvm_timing_begin(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_open = take_event();
+  if (g_open) cudaEventRecord(g_open, st);
+}
+void mvm_timing_end(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if (!g_open) return;
+  cudaEvent_t e = take_event();
+  if (!e) return;
+  cudaEventRecord(e, st);
+  g_pairs.emplace_back(g_open, e);
+  g_open = nullptr;
+}
+}  // namespace gp
+
+extern "C" int64_t gp_launch_count(void) { return (int64_t)gp::g_launches.load(); }
+
+extern "C" void gp_mvm_timing(int32_t enable) { gp::g_timing.store(enable ? 1 : 0); }
+
+extern "C" gp_status gp_mvm_timing_read(double* total_ms, int64_t* products) {
+  std::lock_guard<std::mutex> lk(gp::g_tmu);
+  double tot = 0.0;
+  int64_t cnt = 0;
+  for (auto& pr : gp::g_pairs) {
+    GP_CUDA_TRY(cudaEventSynchronize(pr.second));
+    float ms = 0.f;
+    GP_CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    tot += ms;
+    ++cnt;
+    gp::g_free_events.push_back(pr.first);
+    gp::g_free_events.push_back(pr.second);
+  }
+  gp::g_pairs.clear();
+  if (total_ms) *total_ms = tot;
+  if (products) *products = cnt;
+  return GP_OK;
+}

@@ -400,15 +400,20 @@ gp_status cg_solve(const Prob& pb, MvmOp& mvm, const T* L, int64_t ldl, int k,
   p_start<T><<<(unsigned)cdiv(n * t, 256), 256, 0, st>>>(n, t, g, PinvB, ldpb);
   GP_LAUNCH_CHECK();
 
+  const bool timed = mvm_timing_enabled();
   for (int j = 0; j < o.max_iter; ++j) {
+    if (timed) mvm_timing_begin(st);
     GP_TRY(mvm.apply(g.P, n, t, g.Q, n, g.n_active, st));
+    if (timed) mvm_timing_end(st);
     cg_alpha<T><<<nb, kThreads, 0, st>>>(n, t, j, o.max_iter, g);
     GP_LAUNCH_CHECK();
     const int rec = (R > 0 && (j + 1) % R == 0) ? 1 : 0;
     cg_update<T><<<nb, kThreads, 0, st>>>(n, t, j, o.max_iter, tol2, use_caps, rec, g);
     GP_LAUNCH_CHECK();
     if (rec) {
+      if (timed) mvm_timing_begin(st);
       GP_TRY(mvm.apply(g.X, n, t, g.Q, n, g.n_active, st));
+      if (timed) mvm_timing_end(st);
       cg_resid<T><<<nb, kThreads, 0, st>>>(n, t, j, o.max_iter, tol2, use_caps, g);
       GP_LAUNCH_CHECK();
     }

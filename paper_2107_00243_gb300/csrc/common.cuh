@@ -32,7 +32,12 @@ const char* last_error();
     }                                                                           \
   } while (0)
 
-#define GP_LAUNCH_CHECK() GP_CUDA_TRY(cudaGetLastError())
+void count_launch();
+#define GP_LAUNCH_CHECK()          \
+  do {                             \
+    ::gp::count_launch();          \
+    GP_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
 
 #define GP_REQUIRE(cond, ...)                                                   \
   do {                                                                          \

@@ -110,6 +110,10 @@ struct MvmOp {
                           const int* gate, cudaStream_t st) = 0;
   virtual ~MvmOp() {}
 };
+// Optional CUDA-event timing of the products issued by cg_solve.
+bool mvm_timing_enabled();
+void mvm_timing_begin(cudaStream_t st);
+void mvm_timing_end(cudaStream_t st);
 template <class T>
 gp_status cg_solve(const Prob& pb, MvmOp& mvm, const T* L, int64_t ldl, int k,
                    const double* Cinv, const T* B, int64_t ldb, int t,

@@ -79,6 +79,9 @@ def load():
         "gp_status_string": (ctypes.c_char_p, [i32]),
         "gp_last_error_message": (ctypes.c_char_p, []),
         "gp_rademacher": (i32, [ctypes.c_uint64, i32, i64, i32, vp, vp]),
+        "gp_launch_count": (i64, []),
+        "gp_mvm_timing": (None, [i32]),
+        "gp_mvm_timing_read": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -301,3 +304,20 @@ def gp_rademacher(seed, stream_id, rows, cols, device="cuda"):
     _check("gp_rademacher", lib.gp_rademacher(int(seed), int(stream_id), int(rows), int(cols),
                                               _ptr(out), _stream()))
     return out.t()
+
+
+def launch_count():
+    """Kernels launched by the library since it was loaded."""
+    return int(load().gp_launch_count())
+
+
+def mvm_timing(enable):
+    load().gp_mvm_timing(1 if enable else 0)
+
+
+def mvm_timing_read():
+    """(total ms, number of kernel-matrix products) timed since the last read."""
+    ms = ctypes.c_double(0.0)
+    cnt = ctypes.c_int64(0)
+    _check("gp_mvm_timing_read", load().gp_mvm_timing_read(ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
