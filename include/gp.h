@@ -196,6 +196,15 @@ const char* gp_status_string(int32_t status);
 /* Detail of the last host-side validation failure on this thread (static storage). */
 const char* gp_last_error_message(void);
 
+/* Diagnostic for the tensor-core product (precision GP_BF16): computes W exactly
+ * as gp_kernel_mvm does and also copies the FP32 exponent tile S of the first
+ * 128 x 128 (row, column) tile pair to S_out (device, 128 x 128 row-major):
+ * S_ij = log2(e) (-r_ij^2 / 2) + log2(s) for RBF, -r_ij^2 / 2 for Matern.  The
+ * workspace is that of GP_FN_KERNEL_MVM.  Asynchronous.                          */
+gp_status gp_tc_exponent_tile(const gp_problem* prob, const void* V, int64_t ldv, int32_t t,
+                              void* W, int64_t ldw, float* S_out, void* ws, size_t ws_bytes,
+                              gp_stream_t stream);
+
 /* Instrumentation.  gp_launch_count: kernels this library has launched since it
  * was loaded (host-side count of launch sites).  gp_mvm_timing(1) makes the CG
  * loop of gp_mbcg / gp_mll_and_grad bracket every kernel-matrix product with CUDA

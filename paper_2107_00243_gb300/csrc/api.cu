@@ -78,6 +78,7 @@ void plan_mvm(Arena& A, const Prob& pb, int t, MvmPlan& P) {
     P.tc.norms = A.take<float>((size_t)pb.n);
     P.tc.vpack = A.take<char>(tc_vpack_bytes(pb.n, t, pb.prec));
     P.tc.part = A.take<float>(tc_part_elems(pb.n, t));
+    P.tc.err = A.take<int>(4);
   } else {
     P.scratch = A.take<char>(elem_size(pb.prec) * simt_scratch_elems(pb.n, t));
   }
@@ -182,6 +183,7 @@ gp_status run_kernel_mvm(const Prob& pb, const void* V, int64_t ldv, int t, void
                          MvmPlan& P, cudaStream_t st) {
   GP_TRY(run_prep<T>(pb, P.prep, st));
   if (P.use_tc) {
+    GP_CUDA_TRY(cudaMemsetAsync(P.tc.err, 0, 4 * sizeof(int), st));
     GP_TRY(tc_prepare_inputs(pb, P.prep.pr.Xs, P.tc, st));
     TcMvm op;
     op.pb = pb;
@@ -308,6 +310,7 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   // S5-S7: mBCG
   int host_status = 0;
   if (P.mvm.use_tc) {
+    GP_CUDA_TRY(cudaMemsetAsync(P.mvm.tc.err, 0, 4 * sizeof(int), st));
     GP_TRY(tc_prepare_inputs(pb, Xs, P.mvm.tc, st));
     TcMvm op;
     op.pb = pb;
@@ -343,11 +346,17 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
                              nullptr, out, iout);
   GP_LAUNCH_CHECK();
 
-  int hstat = 0, hrank = 0;
+  int hstat = 0, hrank = 0, herr[2] = {0, 0};
   GP_CUDA_TRY(cudaMemcpyAsync(&hstat, P.cg.status, sizeof(int), cudaMemcpyDeviceToHost, st));
   GP_CUDA_TRY(cudaMemcpyAsync(&hrank, P.rank, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (P.mvm.use_tc)
+    GP_CUDA_TRY(cudaMemcpyAsync(herr, P.mvm.tc.err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   GP_CUDA_TRY(cudaStreamSynchronize(st));
   GP_CUDA_TRY(cudaGetLastError());
+  if (herr[0] < 0) {
+    set_error("tensor-core product gave up waiting (site %d)", herr[1]);
+    return (gp_status)herr[0];
+  }
   if (hstat < 0) return (gp_status)hstat;
   if (hrank < k) return GP_WARN_RANK_DEFICIENT;
   return GP_OK;
@@ -566,6 +575,7 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
                        cb.status, st));
   int host_status = 0;
   if (mp.use_tc) {
+    GP_CUDA_TRY(cudaMemsetAsync(mp.tc.err, 0, 4 * sizeof(int), st));
     GP_TRY(tc_prepare_inputs(pb, mp.prep.pr.Xs, mp.tc, st));
     TcMvm op;
     op.pb = pb;
@@ -587,9 +597,15 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
   GP_CUDA_TRY(cudaMemcpyAsync(rho0, cb.rho0, sizeof(double) * t, cudaMemcpyDeviceToDevice, st));
   GP_CUDA_TRY(cudaMemcpyAsync(iters, cb.iters, sizeof(int) * t, cudaMemcpyDeviceToDevice, st));
   GP_CUDA_TRY(cudaMemcpyAsync(status, cb.status, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  int hs = 0;
+  int hs = 0, herr[2] = {0, 0};
   GP_CUDA_TRY(cudaMemcpyAsync(&hs, cb.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (mp.use_tc)
+    GP_CUDA_TRY(cudaMemcpyAsync(herr, mp.tc.err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   GP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr[0] < 0) {
+    set_error("tensor-core product gave up waiting (site %d)", herr[1]);
+    return (gp_status)herr[0];
+  }
   if (hs < 0) return (gp_status)hs;
   return GP_OK;
 }
@@ -720,4 +736,27 @@ extern "C" gp_status gp_mvm_timing_read(double* total_ms, int64_t* products) {
   if (total_ms) *total_ms = tot;
   if (products) *products = cnt;
   return GP_OK;
+}
+
+extern "C" gp_status gp_tc_exponent_tile(const gp_problem* prob, const void* V, int64_t ldv,
+                                         int32_t t, void* W, int64_t ldw, float* S_out, void* ws,
+                                         size_t ws_bytes, gp_stream_t stream) {
+  GP_TRY(check_problem(prob));
+  GP_REQUIRE(prob->precision == GP_BF16, "gp_tc_exponent_tile needs precision GP_BF16");
+  GP_REQUIRE(t >= 1 && t <= kMaxT, "t=%d out of range", t);
+  GP_REQUIRE(V && W && S_out, "NULL pointer");
+  GP_REQUIRE(ldv >= prob->n && ldw >= prob->n, "leading dimensions must be >= n");
+  Prob pb = make_prob(prob);
+  GP_REQUIRE(tc_supported(pb, t), "tensor-core precision does not support this shape");
+  GP_TRY(check_ws(ws, ws_bytes, gp_workspace_size(GP_FN_KERNEL_MVM, pb.n, pb.d, 0, t, pb.prec, 1)));
+  Arena A;
+  A.base = static_cast<char*>(ws);
+  MvmPlan P;
+  plan_mvm(A, pb, t, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  GP_TRY(run_prep<float>(pb, P.prep, st));
+  GP_CUDA_TRY(cudaMemsetAsync(P.tc.err, 0, 4 * sizeof(int), st));
+  GP_TRY(tc_prepare_inputs(pb, P.prep.pr.Xs, P.tc, st));
+  return kmvm_tc_debug(pb, P.tc, static_cast<const float*>(V), ldv, t, static_cast<float*>(W),
+                       ldw, nullptr, S_out, st);
 }

@@ -1,22 +1,673 @@
-// Tensor-core (tcgen05) kernel-matrix products for the TF32 / BF16 precisions.
+// Tensor-core (tcgen05 / TMEM) kernel-matrix product for the BF16 precision:
+//   W = (K + sigma^2 I) V,  computed tile by tile like fused attention without the
+//   softmax normalisation (K is never stored):
+//
+//   GEMM1  S = A_I B_J^T          (128 x 128 per tile, FP32 in TMEM)
+//          A_i = [c x_i, 1, -c |x_i|^2 / 2],  B_j = [x_j, -c |x_j|^2 / 2 + b, 1]
+//          so S_ij = c (x_i . x_j - |x_i|^2/2 - |x_j|^2/2) + b = -c r_ij^2 / 2 + b.
+//          RBF: c = log2(e), b = log2(s)  ->  k_ij = 2^S_ij.
+//          Matern: c = 1, b = 0           ->  r = sqrt(-2 S), k = s poly(r) e^{-a r}.
+//          Each operand is split into BF16 hi + lo parts and the product is formed as
+//          hi.hi + hi.lo + lo.hi, which keeps ~16 significant bits in S despite the
+//          cancellation between the norms and the dot product.
+//   epilogue  P = k(S) in FP32 registers, rounded to BF16 and written back into the
+//          same TMEM columns (tcgen05.ld / tcgen05.st, one thread per row).
+//   GEMM2  O_I += P V_J           (A = P from TMEM, B = V tile from shared memory)
+//
+// Roles of a CTA (persistent over (row tile, column chunk) work units):
+//   warp 0      producer: bulk TMA copies (cp.async.bulk) of pre-tiled operand tiles
+//   warp 1      TMEM allocator and single-thread MMA issuer
+//   warps 2-5   epilogue warpgroup (TMEM lanes 32 (w % 4) .. + 31)
+// Synchronisation uses mbarriers; every wait gives up after a time limit, sets an
+// abort flag and an error code, and the CTA drains its own copies and MMAs (again
+// with a limit) before freeing TMEM and returning.
+//
+// Operands are laid out in HBM by the pack kernels below in the canonical
+// no-swizzle K-major UMMA layout: 8-row x 16-byte core matrices, core matrices
+// adjacent along K 128 bytes apart (leading byte offset), 8-row groups
+// (K/8) * 128 bytes apart (stride byte offset).  Each 128-row tile is one
+// contiguous block, so one bulk copy moves it.
 #include "ops.h"
 
-namespace gp {
+#include <cuda_bf16.h>
 
-size_t tc_xpack_bytes(int64_t n, int d, int prec) { (void)n; (void)d; (void)prec; return 0; }
-size_t tc_vpack_bytes(int64_t n, int t, int prec) { (void)n; (void)t; (void)prec; return 0; }
-size_t tc_part_elems(int64_t n, int t) { (void)n; (void)t; return 0; }
-bool tc_supported(const Prob& pb, int t) { (void)pb; (void)t; return false; }
-gp_status tc_prepare_inputs(const Prob& pb, const void* Xs, const TcBufs& tb, cudaStream_t st) {
-  (void)pb; (void)Xs; (void)tb; (void)st;
-  set_error("tensor-core path not available");
-  return GP_ERR_INVALID_ARG;
+namespace gp {
+namespace {
+
+constexpr int BM = 128;        // rows per tile (MMA M)
+constexpr int BN = 128;        // columns per tile (GEMM1 N, GEMM2 K)
+constexpr int STAGES = 3;
+constexpr int kThreads = 192;  // 6 warps
+constexpr long long kWaitNs = 2000000000LL;   // 2 s per wait before giving up
+
+// ---- PTX wrappers -------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+      "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity; false on abort or time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          int* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (gtime() - t0 > (unsigned long long)kWaitNs) {
+      *abort = 1;
+      atomicExch(err, (int)GP_ERR_DEVICE_TIMEOUT);
+      atomicExch(err + 1, code);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+#define GP_TMEM_LD32(taddr, v)                                                                 \
+  asm volatile(                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"        \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),   \
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),            \
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),         \
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),         \
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),         \
+        "=r"(v[31])                                                                            \
+      : "r"(taddr))
+#define GP_TMEM_ST16(taddr, v)                                                                  \
+  asm volatile(                                                                                 \
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"   \
+      "%13,%14,%15,%16};" ::"r"(taddr),                                                         \
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), \
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),       \
+      "r"(v[15])                                                                                \
+      : "memory")
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major (sm_100 format, version 1).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row r, k) inside a tile of `kcols` K-elements (bf16).
+__host__ __device__ __forceinline__ uint32_t tile_off(int r, int k, int kcols) {
+  return (uint32_t)((r >> 3) * (kcols * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+struct TcArgs {
+  const __nv_bfloat16* xa;   // ntiles tiles of BM x kx (A form)
+  const __nv_bfloat16* xb;   // ntiles tiles of BN x kx (B form)
+  const __nv_bfloat16* vp;   // ntiles tiles of tp x BN
+  float* part;               // nchunks x tp x npad
+  int n, npad, ntiles, nchunks, tiles_per_chunk, kx, tp, t, kind, D;
+  const double* theta;       // device hyperparameters (output scale for Matern)
+  const int* gate;
+  int* err;                  // err[0] = status, err[1] = where a wait gave up
+  float* dbg;                // optional: S of the first tile of unit 0
+};
+
+struct __align__(8) Bars {
+  unsigned long long full[STAGES], empty[STAGES];
+  unsigned long long a_full, a_free, s_full[2], s_free[2], p_ready[2], o_full, o_free, drain;
+  unsigned int tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ float kernel_from_s(int kind, float sv, float s) {
+  if (kind == GP_RBF) return ex2(sv);
+  float r2 = fmaxf(-2.0f * sv, 0.0f);
+  float r = sqrtf(r2);
+  const float L2E = 1.4426950408889634f;
+  if (kind == GP_MATERN32) {
+    float ar = 1.7320508075688772f * r;
+    return s * (1.0f + ar) * ex2(-ar * L2E);
+  }
+  float ar = 2.23606797749979f * r;
+  return s * (1.0f + ar + 1.6666666666666667f * r2) * ex2(-ar * L2E);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
+  if (g.gate && *g.gate == 0) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kx = g.kx, tp = g.tp;
+  const uint32_t a_bytes = BM * kx * 2, b_bytes = BN * kx * 2, v_bytes = tp * BN * 2;
+  unsigned char* sA = smem;
+  unsigned char* sB = sA + a_bytes;
+  unsigned char* sV = sB + STAGES * b_bytes;
+  Bars* bars = reinterpret_cast<Bars*>(sV + STAGES * v_bytes);
+  volatile int* abort = &bars->abort;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 1);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bars->a_full), 1);
+    mbar_init(smem_u32(&bars->a_free), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bars->s_full[b]), 1);
+      mbar_init(smem_u32(&bars->s_free[b]), 1);
+      mbar_init(smem_u32(&bars->p_ready[b]), BM);
+    }
+    mbar_init(smem_u32(&bars->o_full), 1);
+    mbar_init(smem_u32(&bars->o_free), BM);
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(&bars->tmem_base), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  // TMEM columns: S/P buffers at 0 and 128, O accumulator at 256.
+  const uint32_t t_s[2] = {tmem, tmem + 128};
+  const uint32_t t_o = tmem + 256;
+  const int nunits = g.ntiles * g.nchunks;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t gtile = 0, a_par = 0, a_arms = 0;
+      int armed[STAGES] = {0, 0, 0};
+      uint32_t arm_par[STAGES] = {0, 0, 0};
+      bool first = true;
+      for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
+        const int rt = u / g.nchunks, ch = u % g.nchunks;
+        const int j0 = ch * g.tiles_per_chunk;
+        const int j1 = min(g.ntiles, j0 + g.tiles_per_chunk);
+        if (!first && !mbar_wait(smem_u32(&bars->a_free), a_par, abort, g.err, 11)) break;
+        if (!first) a_par ^= 1;
+        first = false;
+        mbar_expect_tx(smem_u32(&bars->a_full), a_bytes);
+        bulk_g2s(smem_u32(sA), reinterpret_cast<const unsigned char*>(g.xa) + (size_t)rt * a_bytes,
+                 a_bytes, smem_u32(&bars->a_full));
+        ++a_arms;
+        for (int j = j0; j < j1; ++j, ++gtile) {
+          const int st = gtile % STAGES;
+          const uint32_t ph = (gtile / STAGES) & 1;
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort, g.err, 12)) break;
+          const uint32_t fb = smem_u32(&bars->full[st]);
+          mbar_expect_tx(fb, b_bytes + v_bytes);
+          bulk_g2s(smem_u32(sB + st * b_bytes),
+                   reinterpret_cast<const unsigned char*>(g.xb) + (size_t)j * b_bytes, b_bytes, fb);
+          bulk_g2s(smem_u32(sV + st * v_bytes),
+                   reinterpret_cast<const unsigned char*>(g.vp) + (size_t)j * v_bytes, v_bytes, fb);
+          armed[st] = 1;
+          arm_par[st] = ph;
+        }
+      }
+      if (*abort) {
+        // drain: every copy this thread issued must land before the CTA exits
+        for (int st = 0; st < STAGES; ++st) {
+          if (!armed[st]) continue;
+          const unsigned long long t0 = gtime();
+          while (!mbar_try_wait(smem_u32(&bars->full[st]), arm_par[st]) &&
+                 gtime() - t0 < (unsigned long long)kWaitNs) {
+          }
+        }
+        if (a_arms > 0) {
+          const unsigned long long t0 = gtime();
+          while (!mbar_try_wait(smem_u32(&bars->a_full), (a_arms - 1) & 1) &&
+                 gtime() - t0 < (unsigned long long)kWaitNs) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id1 = idesc_bf16(BM, BN);
+      const uint32_t id2 = idesc_bf16(BM, tp);
+      uint32_t gtile = 0, a_par = 0, o_par = 0;
+      uint32_t sf_par[2] = {0, 0}, pr_par[2] = {0, 0};
+      bool first_unit = true;
+      for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
+        const int ch = u % g.nchunks;
+        const int j0 = ch * g.tiles_per_chunk;
+        const int j1 = min(g.ntiles, j0 + g.tiles_per_chunk);
+        const int nt = j1 - j0;
+        if (!mbar_wait(smem_u32(&bars->a_full), a_par, abort, g.err, 21)) break;
+        a_par ^= 1;
+        tc_fence_after();
+        uint32_t prev_stage = 0, prev_buf = 0;
+        bool ok = true;
+        for (int jj = 0; jj <= nt && ok; ++jj) {
+          if (jj < nt) {
+            const uint32_t st = gtile % STAGES;
+            const uint32_t ph = (gtile / STAGES) & 1;
+            const uint32_t buf = gtile & 1;
+            if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort, g.err, 22)) { ok = false; break; }
+            if (!mbar_wait(smem_u32(&bars->s_free[buf]), sf_par[buf] ^ 1, abort, g.err, 23)) {
+              ok = false;
+              break;
+            }
+            sf_par[buf] ^= 1;
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + st * b_bytes);
+            for (int kk = 0; kk < kx / 16; ++kk)
+              mma_ss(t_s[buf], sdesc(a0 + kk * 256, 128, kx * 16), sdesc(b0 + kk * 256, 128, kx * 16),
+                     id1, kk > 0 ? 1u : 0u);
+            mma_commit(smem_u32(&bars->s_full[buf]));
+            if (jj == nt - 1) mma_commit(smem_u32(&bars->a_free));
+          }
+          if (jj > 0) {
+            // GEMM2 for the previous tile
+            const uint32_t pbuf = prev_buf;
+            if (!mbar_wait(smem_u32(&bars->p_ready[pbuf]), pr_par[pbuf], abort, g.err, 24)) {
+              ok = false;
+              break;
+            }
+            pr_par[pbuf] ^= 1;
+            if (jj == 1) {
+              // O is overwritten by this unit's first product: wait until the
+              // epilogue has read the previous unit's O
+              if (!first_unit &&
+                  !mbar_wait(smem_u32(&bars->o_free), o_par, abort, g.err, 25)) {
+                ok = false;
+                break;
+              }
+              if (!first_unit) o_par ^= 1;
+            }
+            tc_fence_after();
+            const uint32_t v0 = smem_u32(sV + prev_stage * v_bytes);
+            for (int kk = 0; kk < BN / 16; ++kk)
+              mma_ts(t_o, t_s[pbuf] + kk * 8, sdesc(v0 + kk * 256, 128, BN * 16), id2,
+                     (jj > 1 || kk > 0) ? 1u : 0u);
+            mma_commit(smem_u32(&bars->empty[prev_stage]));
+            mma_commit(smem_u32(&bars->s_free[pbuf]));
+            if (jj == nt) mma_commit(smem_u32(&bars->o_full));
+          }
+          if (jj < nt) {
+            prev_stage = gtile % STAGES;
+            prev_buf = gtile & 1;
+            ++gtile;
+          }
+        }
+        first_unit = false;
+        if (!ok) break;
+      }
+      // drain: a final commit completes once every MMA this thread issued is done
+      mma_commit(smem_u32(&bars->drain));
+      const unsigned long long t0 = gtime();
+      while (!mbar_try_wait(smem_u32(&bars->drain), 0) &&
+             gtime() - t0 < (unsigned long long)kWaitNs) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warpgroup
+    const int quarter = warp & 3;                 // TMEM lane quarter of this warp
+    const int row = quarter * 32 + lane;          // row within the tile
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const float kscale = (float)g.theta[g.D];
+    uint32_t gtile = 0, of_par = 0;
+    uint32_t sfull_par[2] = {0, 0};
+    for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
+      const int rt = u / g.nchunks, ch = u % g.nchunks;
+      const int j0 = ch * g.tiles_per_chunk;
+      const int j1 = min(g.ntiles, j0 + g.tiles_per_chunk);
+      bool ok = true;
+      for (int j = j0; j < j1; ++j, ++gtile) {
+        const uint32_t buf = gtile & 1;
+        if (!mbar_wait(smem_u32(&bars->s_full[buf]), sfull_par[buf], abort, g.err, 31)) {
+          ok = false;
+          break;
+        }
+        sfull_par[buf] ^= 1;
+        tc_fence_after();
+        const uint32_t tb = t_s[buf] + lane_off;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t v[32];
+          GP_TMEM_LD32(tb + c0, v);
+          tmem_wait_ld();
+          if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
+            for (int q = 0; q < 32; ++q) g.dbg[row * BN + c0 + q] = __uint_as_float(v[q]);
+          }
+          uint32_t pk[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            float p0 = kernel_from_s(g.kind, __uint_as_float(v[2 * q]), kscale);
+            float p1 = kernel_from_s(g.kind, __uint_as_float(v[2 * q + 1]), kscale);
+            pk[q] = pack_bf16(p0, p1);
+          }
+          GP_TMEM_ST16(tb + (c0 >> 1), pk);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bars->p_ready[buf]));
+      }
+      if (!ok) break;
+      // the unit's product is complete: O -> partial output
+      if (!mbar_wait(smem_u32(&bars->o_full), of_par, abort, g.err, 32)) break;
+      of_par ^= 1;
+      tc_fence_after();
+      const int grow = rt * BM + row;
+      float* dst = g.part + (size_t)ch * tp * g.npad;
+#pragma unroll 1
+      for (int c0 = 0; c0 < tp; c0 += 32) {
+        uint32_t v[32];
+        if (c0 + 32 <= tp) {
+          GP_TMEM_LD32(t_o + lane_off + c0, v);
+          tmem_wait_ld();
+          for (int q = 0; q < 32; ++q)
+            if (c0 + q < g.t && grow < g.n) dst[(size_t)(c0 + q) * g.npad + grow] = __uint_as_float(v[q]);
+        } else {
+          // tp is a multiple of 16: a final half chunk
+          uint32_t w16[32];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15}, [%16];"
+              : "=r"(w16[0]), "=r"(w16[1]), "=r"(w16[2]), "=r"(w16[3]), "=r"(w16[4]),
+                "=r"(w16[5]), "=r"(w16[6]), "=r"(w16[7]), "=r"(w16[8]), "=r"(w16[9]),
+                "=r"(w16[10]), "=r"(w16[11]), "=r"(w16[12]), "=r"(w16[13]), "=r"(w16[14]),
+                "=r"(w16[15])
+              : "r"(t_o + lane_off + c0));
+          tmem_wait_ld();
+          for (int q = 0; q < 16; ++q)
+            if (c0 + q < g.t && grow < g.n) dst[(size_t)(c0 + q) * g.npad + grow] = __uint_as_float(w16[q]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&bars->o_free));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---- packing kernels ------------------------------------------------------------------
+// Augmented exponent operands, hi/lo split, in the canonical tile layout.
+// A_i = [c x, 1, -c |x|^2/2] ; B_j = [x, -c |x|^2/2 + b, 1]; A' = [A_hi, A_hi, A_lo],
+// B' = [B_hi, B_lo, B_hi], zero padded to kx.
+__global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __restrict__ Xs,
+                              int kind, const double* __restrict__ theta, int D,
+                              __nv_bfloat16* __restrict__ xa, __nv_bfloat16* __restrict__ xb,
+                              float* __restrict__ norms) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntiles * BM) return;
+  const double c = (kind == GP_RBF) ? 1.4426950408889634 : 1.0;
+  const double b = (kind == GP_RBF) ? log2(theta[D]) : 0.0;
+  const int L = d + 2;
+  double av[kMaxD + 2], bv[kMaxD + 2];
+  double nrm = 0.0;
+  const bool valid = i < n;
+  for (int q = 0; q < d; ++q) {
+    double x = valid ? (double)Xs[(size_t)i * d + q] : 0.0;
+    nrm += x * x;
+    av[q] = c * x;
+    bv[q] = x;
+  }
+  av[d] = valid ? 1.0 : 0.0;
+  av[d + 1] = valid ? -0.5 * c * nrm : 0.0;
+  bv[d] = valid ? (-0.5 * c * nrm + b) : 0.0;
+  bv[d + 1] = valid ? 1.0 : 0.0;
+  if (valid) norms[i] = (float)nrm;
+  const int tile = i / BM, r = i % BM;
+  unsigned char* ta = reinterpret_cast<unsigned char*>(xa) + (size_t)tile * BM * kx * 2;
+  unsigned char* tb = reinterpret_cast<unsigned char*>(xb) + (size_t)tile * BN * kx * 2;
+  for (int k = 0; k < kx; ++k) {
+    float va = 0.f, vb = 0.f;
+    int seg = k / L, q = k % L;
+    if (seg < 3) {
+      double x = av[q], y = bv[q];
+      float xh = __bfloat162float(__float2bfloat16_rn((float)x));
+      float yh = __bfloat162float(__float2bfloat16_rn((float)y));
+      float xl = (float)(x - (double)xh), yl = (float)(y - (double)yh);
+      va = (seg == 2) ? xl : xh;        // [hi, hi, lo]
+      vb = (seg == 1) ? yl : yh;        // [hi, lo, hi]
+    }
+    *reinterpret_cast<__nv_bfloat16*>(ta + tile_off(r, k, kx)) = __float2bfloat16_rn(va);
+    *reinterpret_cast<__nv_bfloat16*>(tb + tile_off(r, k, kx)) = __float2bfloat16_rn(vb);
+  }
+}
+
+// V (n x t FP32, column-major) -> tiles of tp x BN BF16 (rows = columns of V).
+__global__ void pack_v_kernel(int n, int ntiles, int t, int tp, const float* __restrict__ V,
+                              int64_t ldv, __nv_bfloat16* __restrict__ vp, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)ntiles * BN * tp;
+  if (e >= total) return;
+  const int j = (int)(e % ((int64_t)ntiles * BN));
+  const int c = (int)(e / ((int64_t)ntiles * BN));
+  const float v = (j < n && c < t) ? V[j + (int64_t)c * ldv] : 0.f;
+  const int tile = j / BN, k = j % BN;
+  unsigned char* tv = reinterpret_cast<unsigned char*>(vp) + (size_t)tile * tp * BN * 2;
+  *reinterpret_cast<__nv_bfloat16*>(tv + tile_off(c, k, BN)) = __float2bfloat16_rn(v);
+}
+
+// W = sum over chunks + sigma^2 V (NaN on a device-side abort).
+__global__ void tc_reduce_kernel(int n, int npad, int t, int tp, int nchunks,
+                                 const float* __restrict__ part,
+                                 const float* __restrict__ V, int64_t ldv,
+                                 const double* __restrict__ theta, int D, float* __restrict__ W,
+                                 int64_t ldw, const int* gate, const int* err) {
+  if (gate && *gate == 0) return;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * t) return;
+  const int c = (int)(e / n), i = (int)(e % n);
+  float acc = 0.f;
+  for (int ch = 0; ch < nchunks; ++ch) acc += part[((size_t)ch * tp + c) * npad + i];
+  acc = fmaf((float)theta[D + 1], V[i + (int64_t)c * ldv], acc);
+  if (*err) acc = __int_as_float(0x7fc00000);
+  W[i + (int64_t)c * ldw] = acc;
+}
+
+int sm_count() {
+  static int cnt = 0;
+  if (cnt == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&cnt, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || cnt <= 0)
+      cnt = 148;
+  }
+  return cnt;
+}
+
+int kx_for(int d) { return 3 * (d + 2) <= 64 ? 64 : 128; }
+int tp_for(int t) { return (t + 15) / 16 * 16; }
+int ntiles_for(int64_t n) { return (int)cdiv(n, BM); }
+int nchunks_for(int ntiles) {
+  int want = (int)cdiv(8LL * 152, ntiles);
+  int maxc = std::max(1, ntiles / 16);
+  return std::max(1, std::min(want, maxc));
+}
+size_t smem_bytes(int kx, int tp) {
+  size_t b = (size_t)BM * kx * 2 + (size_t)STAGES * BN * kx * 2 + (size_t)STAGES * tp * BN * 2 +
+             sizeof(Bars) + 1024;
+  // keep one CTA per SM: it owns all 512 TMEM columns
+  return std::max<size_t>(b, 120 * 1024);
+}
+
+}  // namespace
+
+size_t tc_xpack_bytes(int64_t n, int d, int prec) {
+  (void)prec;
+  return (size_t)ntiles_for(n) * BM * kx_for(d) * 2 * 2;   // A and B forms
+}
+size_t tc_vpack_bytes(int64_t n, int t, int prec) {
+  (void)prec;
+  return (size_t)ntiles_for(n) * BN * tp_for(t) * 2;
+}
+size_t tc_part_elems(int64_t n, int t) {
+  const int nt = ntiles_for(n);
+  return (size_t)nchunks_for(nt) * tp_for(t) * nt * BM;
+}
+bool tc_supported(const Prob& pb, int t) {
+  return pb.prec == GP_BF16 && t >= 1 && t <= 64 && pb.d <= kMaxD;
+}
+
+gp_status tc_prepare_inputs(const Prob& pb, const void* Xs, const TcBufs& tb, cudaStream_t st) {
+  const int nt = ntiles_for(pb.n), kx = kx_for(pb.d);
+  __nv_bfloat16* xa = static_cast<__nv_bfloat16*>(tb.xpack);
+  __nv_bfloat16* xb = xa + (size_t)nt * BM * kx;
+  pack_x_kernel<<<(unsigned)cdiv((int64_t)nt * BM, 128), 128, 0, st>>>(
+      (int)pb.n, nt, pb.d, kx, static_cast<const float*>(Xs), pb.kind, pb.theta, pb.D, xa, xb,
+      tb.norms);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
 gp_status kmvm_tc(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t, float* W,
                   int64_t ldw, const int* gate, cudaStream_t st) {
-  (void)pb; (void)tb; (void)V; (void)ldv; (void)t; (void)W; (void)ldw; (void)gate; (void)st;
-  set_error("tensor-core path not available");
-  return GP_ERR_INVALID_ARG;
+  return kmvm_tc_debug(pb, tb, V, ldv, t, W, ldw, gate, nullptr, st);
+}
+
+gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
+                        float* W, int64_t ldw, const int* gate, float* dbg, cudaStream_t st) {
+  const int n = (int)pb.n;
+  const int nt = ntiles_for(pb.n), kx = kx_for(pb.d), tp = tp_for(t);
+  const int nch = nchunks_for(nt);
+  const int npad = nt * BM;
+  __nv_bfloat16* xa = static_cast<__nv_bfloat16*>(tb.xpack);
+  __nv_bfloat16* xb = xa + (size_t)nt * BM * kx;
+  __nv_bfloat16* vp = static_cast<__nv_bfloat16*>(tb.vpack);
+  int* err = tb.err;
+  const int64_t vtotal = (int64_t)nt * BN * tp;
+  pack_v_kernel<<<(unsigned)cdiv(vtotal, 256), 256, 0, st>>>(n, nt, t, tp, V, ldv, vp, gate);
+  GP_LAUNCH_CHECK();
+  TcArgs a;
+  a.xa = xa;
+  a.xb = xb;
+  a.vp = vp;
+  a.part = tb.part;
+  a.n = n;
+  a.npad = npad;
+  a.ntiles = nt;
+  a.nchunks = nch;
+  a.tiles_per_chunk = (int)cdiv(nt, nch);
+  a.kx = kx;
+  a.tp = tp;
+  a.t = t;
+  a.kind = pb.kind;
+  a.D = pb.D;
+  a.theta = pb.theta;
+  a.gate = gate;
+  a.err = err;
+  a.dbg = dbg;
+  // the chunk count must not leave an empty chunk
+  a.nchunks = (int)cdiv(nt, a.tiles_per_chunk);
+  const size_t sm = smem_bytes(kx, tp);
+  static bool attr_set = false;
+  if (!attr_set) {
+    GP_CUDA_TRY(cudaFuncSetAttribute(kmvm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(200 * 1024)));
+    attr_set = true;
+  }
+  const int units = nt * a.nchunks;
+  const int grid = std::min(units, sm_count());
+  kmvm_tc_kernel<<<grid, kThreads, sm, st>>>(a);
+  GP_LAUNCH_CHECK();
+  tc_reduce_kernel<<<(unsigned)cdiv((int64_t)n * t, 256), 256, 0, st>>>(
+      n, npad, t, tp, a.nchunks, tb.part, V, ldv, pb.theta, pb.D, W, ldw, gate, err);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
 }
 
 }  // namespace gp

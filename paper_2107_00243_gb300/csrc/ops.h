@@ -39,6 +39,7 @@ struct TcBufs {
   float* norms;      // n
   void* vpack;       // packed right-hand-side tiles
   float* part;       // split partial sums
+  int* err;          // 2 ints: device-side status and the wait that gave up
 };
 size_t tc_xpack_bytes(int64_t n, int d, int prec);
 size_t tc_vpack_bytes(int64_t n, int t, int prec);
@@ -47,6 +48,9 @@ bool tc_supported(const Prob& pb, int t);
 gp_status tc_prepare_inputs(const Prob& pb, const void* Xs, const TcBufs& tb, cudaStream_t st);
 gp_status kmvm_tc(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
                   float* W, int64_t ldw, const int* gate, cudaStream_t st);
+// Same, and (dbg != null) the exponent tile S of the first tile pair -> dbg (128 x 128).
+gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
+                        float* W, int64_t ldw, const int* gate, float* dbg, cudaStream_t st);
 
 // ---- pivoted Cholesky (pivchol.cu) ----------------------------------------------
 struct PivBufs {

@@ -79,6 +79,7 @@ def load():
         "gp_status_string": (ctypes.c_char_p, [i32]),
         "gp_last_error_message": (ctypes.c_char_p, []),
         "gp_rademacher": (i32, [ctypes.c_uint64, i32, i64, i32, vp, vp]),
+        "gp_tc_exponent_tile": (i32, [P, vp, i64, i32, vp, i64, vp, vp, sz, vp]),
         "gp_launch_count": (i64, []),
         "gp_mvm_timing": (None, [i32]),
         "gp_mvm_timing_read": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
@@ -190,6 +191,21 @@ def gp_kernel_mvm(prob, V, workspace=None):
     _check("gp_kernel_mvm", lib.gp_kernel_mvm(prob.cref(), _ptr(Vc), prob.n, t, _ptr(W), prob.n,
                                               _ptr(ws), ws.numel(), _stream()))
     return W.t()
+
+
+def gp_tc_exponent_tile(prob, V, workspace=None):
+    """(W, S): the BF16 tensor-core product and its first 128 x 128 exponent tile."""
+    lib = load()
+    Vc = _colmajor(V, prob.dtype, prob.device)
+    t = Vc.shape[0]
+    W = torch.empty_like(Vc)
+    S = torch.full((128, 128), float("nan"), dtype=torch.float32, device=prob.device)
+    ws = (workspace or _WS).get(gp_workspace_size(FN_KERNEL_MVM, prob.n, prob.d, 0, t,
+                                                  prob.precision), prob.device)
+    _check("gp_tc_exponent_tile",
+           lib.gp_tc_exponent_tile(prob.cref(), _ptr(Vc), prob.n, t, _ptr(W), prob.n, _ptr(S),
+                                   _ptr(ws), ws.numel(), _stream()))
+    return W.t(), S
 
 
 def gp_kernel_grad_mvm(prob, V, workspace=None):
