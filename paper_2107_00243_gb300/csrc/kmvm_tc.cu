@@ -10,9 +10,15 @@
 //          Each operand is split into BF16 hi + lo parts and the product is formed as
 //          hi.hi + hi.lo + lo.hi, which keeps ~16 significant bits in S despite the
 //          cancellation between the norms and the dot product.
-//   epilogue  P = k(S) in FP32 registers, rounded to BF16 and written back into the
-//          same TMEM columns (tcgen05.ld / tcgen05.st, one thread per row).
-//   GEMM2  O_I += P V_J           (A = P from TMEM, B = V tile from shared memory)
+//   epilogue  P = k(S) in FP32 registers, split into BF16 P_hi (written back over the
+//          same TMEM columns) and P_lo = bf16(P - P_hi) (its own TMEM columns);
+//          tcgen05.ld / tcgen05.st, one thread per row.
+//   GEMM2  O_I += P_hi V_hi + P_hi V_lo + P_lo V_hi   (A from TMEM, B = the BF16 hi/lo
+//          parts of the V tile in shared memory).  One BF16 pass is not enough for CG:
+//          with |dP|, |dV| ~ 2^-9 relative, p^T K p of a converged direction
+//          (~sigma^2 |p|^2) drowns in the product's error and CG breaks down; the
+//          three-pass split keeps ~2^-16 relative accuracy at three times the GEMM2
+//          tensor work.
 //
 // Roles of a CTA (persistent over (row tile, column chunk) work units):
 //   warp 0      producer: bulk TMA copies (cp.async.bulk) of pre-tiled operand tiles
@@ -36,7 +42,7 @@ namespace {
 
 constexpr int BM = 128;        // rows per tile (MMA M)
 constexpr int BN = 128;        // columns per tile (GEMM1 N, GEMM2 K)
-constexpr int STAGES = 3;
+constexpr int kMaxStages = 3;
 constexpr int kThreads = 192;  // 6 warps
 constexpr long long kWaitNs = 2000000000LL;   // 2 s per wait before giving up
 
@@ -197,6 +203,8 @@ struct TcArgs {
   const __nv_bfloat16* vp;   // ntiles tiles of tp x BN
   float* part;               // nchunks x tp x npad
   int n, npad, ntiles, nchunks, tiles_per_chunk, kx, tp, t, kind, D;
+  int nst;                   // pipeline stages (2 or 3)
+  int split;                 // 1: P V in one BF16 pass; 3: hi/lo split, three passes
   const double* theta;       // device hyperparameters (output scale for Matern)
   const int* gate;
   int* err;                  // err[0] = status, err[1] = where a wait gave up
@@ -204,7 +212,7 @@ struct TcArgs {
 };
 
 struct __align__(8) Bars {
-  unsigned long long full[STAGES], empty[STAGES];
+  unsigned long long full[kMaxStages], empty[kMaxStages];
   unsigned long long a_full, a_free, s_full[2], s_free[2], p_ready[2], o_full, o_free, drain;
   unsigned int tmem_base;
   int abort;
@@ -227,16 +235,17 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   if (g.gate && *g.gate == 0) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kx = g.kx, tp = g.tp;
-  const uint32_t a_bytes = BM * kx * 2, b_bytes = BN * kx * 2, v_bytes = tp * BN * 2;
+  const int kx = g.kx, tp = g.tp, nst = g.nst, split = g.split;
+  const uint32_t a_bytes = BM * kx * 2, b_bytes = BN * kx * 2, vh_bytes = tp * BN * 2;
+  const uint32_t v_bytes = (split > 1 ? 2u : 1u) * vh_bytes;   // hi (and lo) parts of V
   unsigned char* sA = smem;
   unsigned char* sB = sA + a_bytes;
-  unsigned char* sV = sB + STAGES * b_bytes;
-  Bars* bars = reinterpret_cast<Bars*>(sV + STAGES * v_bytes);
+  unsigned char* sV = sB + nst * b_bytes;
+  Bars* bars = reinterpret_cast<Bars*>(sV + nst * v_bytes);
   volatile int* abort = &bars->abort;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(smem_u32(&bars->full[s]), 1);
       mbar_init(smem_u32(&bars->empty[s]), 1);
     }
@@ -261,17 +270,19 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
-  // TMEM columns: S/P buffers at 0 and 128, O accumulator at 256.
+  // TMEM columns: S / P_hi buffers at 0 and 128, O accumulator at 256 (<= 64
+  // columns), P_lo buffers at 320 and 384.
   const uint32_t t_s[2] = {tmem, tmem + 128};
   const uint32_t t_o = tmem + 256;
+  const uint32_t t_lo[2] = {tmem + 320, tmem + 384};
   const int nunits = g.ntiles * g.nchunks;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       uint32_t gtile = 0, a_par = 0, a_arms = 0;
-      int armed[STAGES] = {0, 0, 0};
-      uint32_t arm_par[STAGES] = {0, 0, 0};
+      int armed[kMaxStages] = {0, 0, 0};
+      uint32_t arm_par[kMaxStages] = {0, 0, 0};
       bool first = true;
       for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
         const int rt = u / g.nchunks, ch = u % g.nchunks;
@@ -285,8 +296,8 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
                  a_bytes, smem_u32(&bars->a_full));
         ++a_arms;
         for (int j = j0; j < j1; ++j, ++gtile) {
-          const int st = gtile % STAGES;
-          const uint32_t ph = (gtile / STAGES) & 1;
+          const int st = gtile % nst;
+          const uint32_t ph = (gtile / nst) & 1;
           if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort, g.err, 12)) break;
           const uint32_t fb = smem_u32(&bars->full[st]);
           mbar_expect_tx(fb, b_bytes + v_bytes);
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
       }
       if (*abort) {
         // drain: every copy this thread issued must land before the CTA exits
-        for (int st = 0; st < STAGES; ++st) {
+        for (int st = 0; st < nst; ++st) {
           if (!armed[st]) continue;
           const unsigned long long t0 = gtime();
           while (!mbar_try_wait(smem_u32(&bars->full[st]), arm_par[st]) &&
@@ -335,8 +346,8 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         bool ok = true;
         for (int jj = 0; jj <= nt && ok; ++jj) {
           if (jj < nt) {
-            const uint32_t st = gtile % STAGES;
-            const uint32_t ph = (gtile / STAGES) & 1;
+            const uint32_t st = gtile % nst;
+            const uint32_t ph = (gtile / nst) & 1;
             const uint32_t buf = gtile & 1;
             if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort, g.err, 22)) { ok = false; break; }
             if (!mbar_wait(smem_u32(&bars->s_free[buf]), sf_par[buf] ^ 1, abort, g.err, 23)) {
@@ -372,15 +383,22 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
             }
             tc_fence_after();
             const uint32_t v0 = smem_u32(sV + prev_stage * v_bytes);
-            for (int kk = 0; kk < BN / 16; ++kk)
+            for (int kk = 0; kk < BN / 16; ++kk)       // P_hi V_hi
               mma_ts(t_o, t_s[pbuf] + kk * 8, sdesc(v0 + kk * 256, 128, BN * 16), id2,
                      (jj > 1 || kk > 0) ? 1u : 0u);
+            if (split > 1) {
+              const uint32_t v1 = v0 + vh_bytes;
+              for (int kk = 0; kk < BN / 16; ++kk)     // P_hi V_lo
+                mma_ts(t_o, t_s[pbuf] + kk * 8, sdesc(v1 + kk * 256, 128, BN * 16), id2, 1u);
+              for (int kk = 0; kk < BN / 16; ++kk)     // P_lo V_hi
+                mma_ts(t_o, t_lo[pbuf] + kk * 8, sdesc(v0 + kk * 256, 128, BN * 16), id2, 1u);
+            }
             mma_commit(smem_u32(&bars->empty[prev_stage]));
             mma_commit(smem_u32(&bars->s_free[pbuf]));
             if (jj == nt) mma_commit(smem_u32(&bars->o_full));
           }
           if (jj < nt) {
-            prev_stage = gtile % STAGES;
+            prev_stage = gtile % nst;
             prev_buf = gtile & 1;
             ++gtile;
           }
@@ -425,14 +443,19 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
           if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
             for (int q = 0; q < 32; ++q) g.dbg[row * BN + c0 + q] = __uint_as_float(v[q]);
           }
-          uint32_t pk[16];
+          uint32_t pk[16], pl[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
-            float p0 = kernel_from_s(g.kind, __uint_as_float(v[2 * q]), kscale);
-            float p1 = kernel_from_s(g.kind, __uint_as_float(v[2 * q + 1]), kscale);
-            pk[q] = pack_bf16(p0, p1);
+            const float p0 = kernel_from_s(g.kind, __uint_as_float(v[2 * q]), kscale);
+            const float p1 = kernel_from_s(g.kind, __uint_as_float(v[2 * q + 1]), kscale);
+            const uint32_t h = pack_bf16(p0, p1);
+            pk[q] = h;
+            // residuals of the BF16 rounding, themselves rounded to BF16
+            const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);
+            pl[q] = pack_bf16(p0 - h0, p1 - h1);
           }
           GP_TMEM_ST16(tb + (c0 >> 1), pk);
+          if (split > 1) GP_TMEM_ST16(t_lo[buf] + lane_off + (c0 >> 1), pl);
         }
         tmem_wait_st();
         tc_fence_before();
@@ -528,8 +551,9 @@ __global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __r
 }
 
 // V (n x t FP32, column-major) -> tiles of tp x BN BF16 (rows = columns of V).
-__global__ void pack_v_kernel(int n, int ntiles, int t, int tp, const float* __restrict__ V,
-                              int64_t ldv, __nv_bfloat16* __restrict__ vp, const int* gate) {
+__global__ void pack_v_kernel(int n, int ntiles, int t, int tp, int split,
+                              const float* __restrict__ V, int64_t ldv,
+                              __nv_bfloat16* __restrict__ vp, const int* gate) {
   if (gate && *gate == 0) return;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)ntiles * BN * tp;
@@ -538,8 +562,13 @@ __global__ void pack_v_kernel(int n, int ntiles, int t, int tp, const float* __r
   const int c = (int)(e / ((int64_t)ntiles * BN));
   const float v = (j < n && c < t) ? V[j + (int64_t)c * ldv] : 0.f;
   const int tile = j / BN, k = j % BN;
-  unsigned char* tv = reinterpret_cast<unsigned char*>(vp) + (size_t)tile * tp * BN * 2;
-  *reinterpret_cast<__nv_bfloat16*>(tv + tile_off(c, k, BN)) = __float2bfloat16_rn(v);
+  const size_t part = (size_t)tp * BN * 2;
+  unsigned char* tv = reinterpret_cast<unsigned char*>(vp) + (size_t)tile * part * (split > 1 ? 2 : 1);
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  *reinterpret_cast<__nv_bfloat16*>(tv + tile_off(c, k, BN)) = hi;
+  if (split > 1)
+    *reinterpret_cast<__nv_bfloat16*>(tv + part + tile_off(c, k, BN)) =
+        __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
 // W = sum over chunks + sigma^2 V (NaN on a device-side abort).
@@ -578,11 +607,15 @@ int nchunks_for(int ntiles) {
   int maxc = std::max(1, ntiles / 16);
   return std::max(1, std::min(want, maxc));
 }
-size_t smem_bytes(int kx, int tp) {
-  size_t b = (size_t)BM * kx * 2 + (size_t)STAGES * BN * kx * 2 + (size_t)STAGES * tp * BN * 2 +
-             sizeof(Bars) + 1024;
+constexpr size_t kSmemCap = 200 * 1024;
+size_t smem_bytes(int kx, int tp, int split, int nst) {
+  size_t b = (size_t)BM * kx * 2 + (size_t)nst * BN * kx * 2 +
+             (size_t)nst * tp * BN * 2 * (split > 1 ? 2 : 1) + sizeof(Bars) + 1024;
   // keep one CTA per SM: it owns all 512 TMEM columns
   return std::max<size_t>(b, 120 * 1024);
+}
+int stages_for(int kx, int tp, int split) {
+  return smem_bytes(kx, tp, split, 3) <= kSmemCap ? 3 : 2;
 }
 
 }  // namespace
@@ -593,7 +626,7 @@ size_t tc_xpack_bytes(int64_t n, int d, int prec) {
 }
 size_t tc_vpack_bytes(int64_t n, int t, int prec) {
   (void)prec;
-  return (size_t)ntiles_for(n) * BN * tp_for(t) * 2;
+  return (size_t)ntiles_for(n) * BN * tp_for(t) * 2 * 2;   // hi and lo parts
 }
 size_t tc_part_elems(int64_t n, int t) {
   const int nt = ntiles_for(n);
@@ -630,7 +663,9 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
   __nv_bfloat16* vp = static_cast<__nv_bfloat16*>(tb.vpack);
   int* err = tb.err;
   const int64_t vtotal = (int64_t)nt * BN * tp;
-  pack_v_kernel<<<(unsigned)cdiv(vtotal, 256), 256, 0, st>>>(n, nt, t, tp, V, ldv, vp, gate);
+  const int split = 3;
+  pack_v_kernel<<<(unsigned)cdiv(vtotal, 256), 256, 0, st>>>(n, nt, t, tp, split, V, ldv, vp,
+                                                              gate);
   GP_LAUNCH_CHECK();
   TcArgs a;
   a.xa = xa;
@@ -648,16 +683,18 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
   a.kind = pb.kind;
   a.D = pb.D;
   a.theta = pb.theta;
+  a.split = split;
+  a.nst = stages_for(kx, tp, split);
   a.gate = gate;
   a.err = err;
   a.dbg = dbg;
   // the chunk count must not leave an empty chunk
   a.nchunks = (int)cdiv(nt, a.tiles_per_chunk);
-  const size_t sm = smem_bytes(kx, tp);
+  const size_t sm = smem_bytes(kx, tp, split, a.nst);
   static bool attr_set = false;
   if (!attr_set) {
     GP_CUDA_TRY(cudaFuncSetAttribute(kmvm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(200 * 1024)));
+                                     (int)kSmemCap));
     attr_set = true;
   }
   const int units = nt * a.nchunks;

@@ -59,11 +59,14 @@ __global__ void logquad_kernel(int c0, int max_iter, const double* __restrict__ 
     const double mu = a[hi] - bb * bb / (dd + copysign(hypot(dd, bb), dd));
     double x = a[lo] - mu, z = b[lo];
     for (int kk = lo; kk < hi; ++kk) {
-      double r = hypot(x, z);
-      double cs = 1.0, sn = 0.0;
-      if (r > 0.0) {
-        cs = x / r;
-        sn = z / r;
+      // entries here stay far from the overflow range, so r = sqrt(x^2 + z^2) directly
+      const double r2 = x * x + z * z;
+      double r = 0.0, cs = 1.0, sn = 0.0;
+      if (r2 > 0.0) {
+        r = sqrt(r2);
+        const double ir = 1.0 / r;
+        cs = x * ir;
+        sn = z * ir;
       }
       if (kk > lo) b[kk - 1] = r;
       const double akk = a[kk], ak1 = a[kk + 1], bk = b[kk];
