@@ -107,7 +107,7 @@ void plan_cg(Arena& A, const Prob& pb, int k, int t, int max_iter, CgBufs<T>& c)
   c.P = A.take<T>(nt);
   c.Q = A.take<T>(nt);
   c.Sp = A.take<T>((size_t)std::max(k, 1) * t);
-  c.atb_part = A.take<double>((size_t)atb_chunks(pb.n) * std::max(k, 1) * t);
+  c.atb_part = A.take<double>(cg_atb_part_elems(pb.n, k, t));
   c.S = A.take<double>((size_t)std::max(k, 1) * t);
   c.rho = A.take<double>(t);
   c.rho0 = A.take<double>(t);

@@ -43,24 +43,34 @@ Dev<T> dev_of(const CgBufs<T>& cb, const T* B, int64_t ldb) {
   return d;
 }
 
+// Each block owns one contiguous chunk of rows; inside it, warp w handles columns
+// w, w + 8, ... so every column is read as coalesced 128-byte segments and reduced
+// with warp shuffles (no block barrier per column).  The last block to finish
+// combines the per-block partials in block order (deterministic).
+__device__ __forceinline__ void row_chunk(int64_t n, int64_t* r0, int64_t* r1) {
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  *r0 = blockIdx.x * per;
+  *r1 = min(n, *r0 + per);
+}
+
 // x = 0, r = b, ||b||^2, caps, active set.
 template <class T>
 __global__ void __launch_bounds__(kThreads) cg_init(int64_t n, int t, int max_iter,
                                                    const int* __restrict__ iters_override,
                                                    Dev<T> g) {
-  __shared__ double sh[32];
-  const int nb = gridDim.x;
-  for (int c = 0; c < t; ++c) {
+  const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t r0, r1;
+  row_chunk(n, &r0, &r1);
+  for (int c = warp; c < t; c += kThreads / 32) {
     double acc = 0.0;
-    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < n;
-         a += (int64_t)nb * kThreads) {
-      T b = g.B[a + c * g.ldb];
+    for (int64_t a = r0 + lane; a < r1; a += 32) {
+      const T b = g.B[a + c * g.ldb];
       g.X[a + c * n] = T(0);
       g.R[a + c * n] = b;
       acc += (double)b * (double)b;
     }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) g.part[c * nb + blockIdx.x] = s;
+    acc = warp_sum(acc);
+    if (lane == 0) g.part[c * nb + blockIdx.x] = acc;
   }
   if (last_block_arrived(g.counter)) {
     __shared__ int cnt;
@@ -90,99 +100,167 @@ __global__ void __launch_bounds__(kThreads) cg_init(int64_t n, int t, int max_it
   }
 }
 
-// Sp[i][c] = sum_m Cinv[i][m] S[m][c] for active columns (FP64 product, stored in T).
-template <class T>
-__global__ void apply_cinv(int k, int t, const double* __restrict__ Cinv, Dev<T> g) {
+// ---- preconditioner P^-1 R = sigma^-2 (R - L C^-1 L^T R) ------------------------------
+// (1) S_part[b] = L[chunk b]^T R[chunk b]: thread m of the block owns row m of S and
+//     keeps the TC columns in registers; L and R row tiles are staged in shared memory.
+constexpr int kLtrRows = 32;
+constexpr int kLtrBlocks = 152;   // one wave; each block reduces ~n/152 rows
+template <class T, int TC>
+__global__ void __launch_bounds__(kThreads) ltr_partial(int64_t n, int t, const T* __restrict__ L,
+                                                       int64_t ldl, int k, Dev<T> g) {
   if (*g.n_active == 0) return;
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= k * t) return;
-  int i = e / t, c = e % t;
+  __shared__ T sL[kLtrRows][kThreads];
+  __shared__ __align__(16) T sR[kLtrRows][TC];
+  int64_t r0, r1;
+  row_chunk(n, &r0, &r1);
+  for (int mb = 0; mb < k; mb += kThreads) {
+    const int m = mb + threadIdx.x;
+    T acc[TC];
+#pragma unroll
+    for (int c = 0; c < TC; ++c) acc[c] = T(0);
+    for (int64_t rb = r0; rb < r1; rb += kLtrRows) {
+      const int rn = (int)min((int64_t)kLtrRows, r1 - rb);
+      __syncthreads();
+      for (int e = threadIdx.x; e < kLtrRows * kThreads; e += kThreads) {
+        const int rr = e % kLtrRows, mm = e / kLtrRows;
+        sL[rr][mm] = (rr < rn && mb + mm < k) ? L[rb + rr + (int64_t)(mb + mm) * ldl] : T(0);
+      }
+      for (int e = threadIdx.x; e < kLtrRows * TC; e += kThreads) {
+        const int rr = e % kLtrRows, c = e / kLtrRows;
+        sR[rr][c] = (rr < rn && c < t) ? g.R[rb + rr + (int64_t)c * n] : T(0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int rr = 0; rr < kLtrRows; ++rr) {
+        const T l = sL[rr][threadIdx.x];
+#pragma unroll
+        for (int c = 0; c < TC; ++c) acc[c] = fma(l, sR[rr][c], acc[c]);
+      }
+    }
+    if (m < k) {
+      double* out = g.S + (size_t)blockIdx.x * k * t;   // per-block partials
+      for (int c = 0; c < t; ++c) out[(size_t)m * t + c] = (double)acc[c];
+    }
+  }
+}
+
+// (2) S = sum of the block partials (FP64), Sp = C^-1 S (FP64), for active columns.
+template <class T>
+__global__ void reduce_cinv(int k, int t, int ldsp, int nparts, const double* __restrict__ Cinv,
+                            const double* __restrict__ part, Dev<T> g) {
+  if (*g.n_active == 0) return;
+  extern __shared__ double sS[];    // k doubles: column c of S
+  const int c = blockIdx.y;
   if (!g.active[c]) return;
+  for (int m = threadIdx.x; m < k; m += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[((size_t)b * k + m) * t + c];
+    sS[m] = s;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
   const double* crow = Cinv + (int64_t)i * k;
   double a0 = 0.0, a1 = 0.0;
   int m = 0;
   for (; m + 1 < k; m += 2) {
-    a0 += crow[m] * g.S[(int64_t)m * t + c];
-    a1 += crow[m + 1] * g.S[(int64_t)(m + 1) * t + c];
+    a0 += crow[m] * sS[m];
+    a1 += crow[m + 1] * sS[m + 1];
   }
-  if (m < k) a0 += crow[m] * g.S[(int64_t)m * t + c];
-  g.Sp[(int64_t)i * t + c] = (T)(a0 + a1);
+  if (m < k) a0 += crow[m] * sS[m];
+  g.Sp[(int64_t)i * ldsp + c] = (T)(a0 + a1);
 }
 
-// z = sigma^-2 (r - L Sp) and rho' = r^T z for active columns.
-//   mode 0 (start): rho = rho0 = rho'
+// (3) z = sigma^-2 (r - L Sp) and the partial sums of r^T z for active columns.
+//   mode 0 (start): rho = rho0 = r^T z
 //   mode 1 (step j): beta_j = rho' / rho, rho = rho'
-constexpr int kPc = 32;   // columns per pass
 constexpr int kPm = 64;   // rows of Sp staged per tile
-template <class T>
-__global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, const T* __restrict__ L,
-                                                       int64_t ldl, int k,
-                                                       const double* __restrict__ theta, int D,
-                                                       int mode, int j, int max_iter, Dev<T> g) {
+template <class T, int TC>
+__global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, int c0,
+                                                       const T* __restrict__ L, int64_t ldl,
+                                                       int k, const double* __restrict__ theta,
+                                                       int D, Dev<T> g) {
   if (*g.n_active == 0) return;
-  __shared__ T ssp[kPm][kPc];
-  __shared__ double sh[32];
-  const int nb = gridDim.x;
+  __shared__ __align__(16) T ssp[kPm][TC];
+  __shared__ double swarp[kThreads / 32][TC];
+  const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tc = min(TC, t - c0);
   const T inv_s2 = (T)(1.0 / theta[D + 1]);
-  for (int c0 = 0; c0 < t; c0 += kPc) {
-    const int tc = min(kPc, t - c0);
-    double rz[kPc];
+  T rz[TC];
 #pragma unroll
-    for (int c = 0; c < kPc; ++c) rz[c] = 0.0;
-    for (int64_t a0 = blockIdx.x * (int64_t)kThreads; a0 < n; a0 += (int64_t)nb * kThreads) {
-      const int64_t a = a0 + threadIdx.x;
-      T acc[kPc];
+  for (int c = 0; c < TC; ++c) rz[c] = T(0);
+  for (int64_t a0 = blockIdx.x * (int64_t)kThreads; a0 < n; a0 += (int64_t)nb * kThreads) {
+    const int64_t a = a0 + threadIdx.x;
+    T acc[TC];
 #pragma unroll
-      for (int c = 0; c < kPc; ++c) acc[c] = T(0);
-      for (int m0 = 0; m0 < k; m0 += kPm) {
-        const int mn = min(kPm, k - m0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < kPm * kPc; e += kThreads) {
-          int mm = e / kPc, c = e % kPc;
-          ssp[mm][c] = (mm < mn && c < tc) ? g.Sp[(int64_t)(m0 + mm) * t + c0 + c] : T(0);
-        }
-        __syncthreads();
-        if (a < n) {
-          for (int mm = 0; mm < mn; ++mm) {
-            const T l = L[a + (int64_t)(m0 + mm) * ldl];
-#pragma unroll
-            for (int c = 0; c < kPc; ++c) acc[c] = fma(l, ssp[mm][c], acc[c]);
-          }
-        }
+    for (int c = 0; c < TC; ++c) acc[c] = T(0);
+    for (int m0 = 0; m0 < k; m0 += kPm) {
+      const int mn = min(kPm, k - m0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < kPm * TC; e += kThreads) {
+        const int mm = e / TC, c = e % TC;
+        ssp[mm][c] = (mm < mn && c < tc) ? g.Sp[(int64_t)(m0 + mm) * t + c0 + c] : T(0);
       }
+      __syncthreads();
       if (a < n) {
+        for (int mm = 0; mm < mn; ++mm) {
+          const T l = L[a + (int64_t)(m0 + mm) * ldl];
 #pragma unroll
-        for (int c = 0; c < kPc; ++c) {
-          if (c < tc && g.active[c0 + c]) {
-            const int64_t off = a + (int64_t)(c0 + c) * n;
-            const T r = g.R[off];
-            const T z = (r - acc[c]) * inv_s2;
-            g.Z[off] = z;
-            rz[c] += (double)r * (double)z;
-          }
+          for (int c = 0; c < TC; ++c) acc[c] = fma(l, ssp[mm][c], acc[c]);
         }
       }
     }
-    for (int c = 0; c < tc; ++c) {
-      if (!g.active[c0 + c]) continue;
-      double s = block_sum(rz[c], sh);
-      if (threadIdx.x == 0) g.part[(c0 + c) * nb + blockIdx.x] = s;
+    if (a < n) {
+#pragma unroll
+      for (int c = 0; c < TC; ++c) {
+        if (c < tc && g.active[c0 + c]) {
+          const int64_t off = a + (int64_t)(c0 + c) * n;
+          const T r = g.R[off];
+          const T z = (r - acc[c]) * inv_s2;
+          g.Z[off] = z;
+          rz[c] = fma(r, z, rz[c]);
+        }
+      }
     }
   }
-  if (last_block_arrived(g.counter)) {
-    for (int c = threadIdx.x; c < t; c += blockDim.x) {
-      if (!g.active[c]) continue;
-      double s = 0.0;
-      for (int b = 0; b < nb; ++b) s += g.part[c * nb + b];
-      if (mode == 0) {
-        g.rho[c] = s;
-        g.rho0[c] = s;
-      } else {
-        double be = s / g.rho[c];
-        if (!isfinite(be)) { *g.status = GP_ERR_NUMERIC; be = 0.0; }
-        g.beta[(int64_t)c * max_iter + j] = be;
-        g.rho[c] = s;
+  // per-column block sums: warp shuffles, then the 8 warp values in order
+#pragma unroll
+  for (int c = 0; c < TC; ++c) {
+    double v = warp_sum((double)rz[c]);
+    if (lane == 0) swarp[warp][c] = v;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < tc; c += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += swarp[w][c];
+    g.part[(c0 + c) * nb + blockIdx.x] = s;
+  }
+}
+
+// Combine the r^T z partials of all column chunks (one small launch).
+template <class T>
+__global__ void rho_combine(int t, int nb, int mode, int j, int max_iter, Dev<T> g) {
+  if (*g.n_active == 0) return;
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    if (!g.active[c]) continue;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += g.part[c * nb + b];
+    if (mode == 0) {
+      g.rho[c] = s;
+      g.rho0[c] = s;
+    } else {
+      if (!(s > 0.0) || !isfinite(s)) {
+        // r^T P^-1 r <= 0 only happens once r is at the rounding floor of the
+        // preconditioner solve: the column stops here (no beta_j, m = j + 1 nodes)
+        g.active[c] = 0;
+        g.iters[c] = j + 1;
+        atomicSub(g.n_active, 1);
+        continue;
       }
+      double be = s / g.rho[c];
+      if (!isfinite(be)) { *g.status = GP_ERR_NUMERIC; be = 0.0; }
+      g.beta[(int64_t)c * max_iter + j] = be;
+      g.rho[c] = s;
     }
   }
 }
@@ -204,16 +282,16 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) cg_alpha(int64_t n, int t, int j, int max_iter,
                                                     Dev<T> g) {
   if (*g.n_active == 0) return;
-  __shared__ double sh[32];
-  const int nb = gridDim.x;
-  for (int c = 0; c < t; ++c) {
+  const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t r0, r1;
+  row_chunk(n, &r0, &r1);
+  for (int c = warp; c < t; c += kThreads / 32) {
     if (!g.active[c]) continue;
     double acc = 0.0;
-    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < n;
-         a += (int64_t)nb * kThreads)
+    for (int64_t a = r0 + lane; a < r1; a += 32)
       acc += (double)g.P[a + c * n] * (double)g.Q[a + c * n];
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) g.part[c * nb + blockIdx.x] = s;
+    acc = warp_sum(acc);
+    if (lane == 0) g.part[c * nb + blockIdx.x] = acc;
   }
   if (last_block_arrived(g.counter)) {
     for (int c = threadIdx.x; c < t; c += blockDim.x) {
@@ -264,24 +342,22 @@ __global__ void __launch_bounds__(kThreads) cg_update(int64_t n, int t, int j, i
                                                      double tol2, int use_caps, int recompute,
                                                      Dev<T> g) {
   if (*g.n_active == 0) return;
-  __shared__ double sh[32];
-  const int nb = gridDim.x;
-  for (int c = 0; c < t; ++c) {
+  const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t r0, r1;
+  row_chunk(n, &r0, &r1);
+  for (int c = warp; c < t; c += kThreads / 32) {
     if (!g.active[c]) continue;
     const T al = (T)g.alpha[(int64_t)c * max_iter + j];
     double acc = 0.0;
-    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < n;
-         a += (int64_t)nb * kThreads) {
+    for (int64_t a = r0 + lane; a < r1; a += 32) {
       const int64_t off = a + c * n;
       g.X[off] = fma(al, g.P[off], g.X[off]);
-      T r = fma(-al, g.Q[off], g.R[off]);
+      const T r = fma(-al, g.Q[off], g.R[off]);
       g.R[off] = r;
       acc += (double)r * (double)r;
     }
-    if (!recompute) {
-      double s = block_sum(acc, sh);
-      if (threadIdx.x == 0) g.part[c * nb + blockIdx.x] = s;
-    }
+    acc = warp_sum(acc);
+    if (lane == 0 && !recompute) g.part[c * nb + blockIdx.x] = acc;
   }
   if (recompute) return;
   if (last_block_arrived(g.counter))
@@ -294,20 +370,20 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) cg_resid(int64_t n, int t, int j, int max_iter,
                                                     double tol2, int use_caps, Dev<T> g) {
   if (*g.n_active == 0) return;
-  __shared__ double sh[32];
-  const int nb = gridDim.x;
-  for (int c = 0; c < t; ++c) {
+  const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t r0, r1;
+  row_chunk(n, &r0, &r1);
+  for (int c = warp; c < t; c += kThreads / 32) {
     if (!g.active[c]) continue;
     double acc = 0.0;
-    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < n;
-         a += (int64_t)nb * kThreads) {
+    for (int64_t a = r0 + lane; a < r1; a += 32) {
       const int64_t off = a + c * n;
-      T r = g.B[a + c * g.ldb] - g.Q[off];
+      const T r = g.B[a + c * g.ldb] - g.Q[off];
       g.R[off] = r;
       acc += (double)r * (double)r;
     }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) g.part[c * nb + blockIdx.x] = s;
+    acc = warp_sum(acc);
+    if (lane == 0) g.part[c * nb + blockIdx.x] = acc;
   }
   if (last_block_arrived(g.counter))
     decide(t, j, g.part, nb, tol2, use_caps, max_iter, g.active, g.caps, g.iters, g.bnorm2,
@@ -365,16 +441,48 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(int64_t n, const T* a, co
   }
 }
 
+int pick_tc(int t) { return t <= 8 ? 8 : t <= 16 ? 16 : t <= 32 ? 32 : t <= 48 ? 48 : 64; }
+
+#define GP_TC_DISPATCH(TCv, ...)                        \
+  switch (TCv) {                                        \
+    case 8: { constexpr int TC = 8; __VA_ARGS__; } break;   \
+    case 16: { constexpr int TC = 16; __VA_ARGS__; } break; \
+    case 32: { constexpr int TC = 32; __VA_ARGS__; } break; \
+    case 48: { constexpr int TC = 48; __VA_ARGS__; } break; \
+    default: { constexpr int TC = 64; __VA_ARGS__; } break; \
+  }
+
 template <class T>
 gp_status precond_apply(int64_t n, int t, const T* L, int64_t ldl, int k, const double* Cinv,
                         const double* theta, int D, int mode, int j, int max_iter,
                         const CgBufs<T>& cb, Dev<T>& g, int nb, cudaStream_t st) {
   if (k > 0) {
-    GP_TRY(atb<T>(n, L, ldl, k, g.R, n, t, cb.atb_part, cb.S, st));
-    apply_cinv<T><<<(unsigned)cdiv((int64_t)k * t, 256), 256, 0, st>>>(k, t, Cinv, g);
+    // L^T R, in column chunks of at most 64
+    const int nbl = (int)std::min<int64_t>(kLtrBlocks, cdiv(n, kLtrRows));
+    for (int c0 = 0; c0 < t; c0 += 64) {
+      const int tc = std::min(64, t - c0);
+      Dev<T> gc = g;                 // this chunk's columns; block partials into atb_part
+      gc.R = g.R + (int64_t)c0 * n;
+      gc.S = cb.atb_part;
+      GP_TC_DISPATCH(pick_tc(tc),
+                     (ltr_partial<T, TC><<<nbl, kThreads, 0, st>>>(n, tc, L, ldl, k, gc)));
+      GP_LAUNCH_CHECK();
+      Dev<T> gs = g;                 // Sp columns c0.. (leading dimension t)
+      gs.active = g.active + c0;
+      gs.Sp = g.Sp + c0;
+      dim3 grid((unsigned)cdiv(k, 128), (unsigned)tc);
+      reduce_cinv<T><<<grid, 128, sizeof(double) * k, st>>>(k, tc, t, nbl, Cinv, cb.atb_part,
+                                                           gs);
+      GP_LAUNCH_CHECK();
+    }
+  }
+  for (int c0 = 0; c0 < t; c0 += 64) {
+    const int tc = std::min(64, t - c0);
+    GP_TC_DISPATCH(pick_tc(tc), (precond_rho<T, TC><<<nb, kThreads, 0, st>>>(
+                                    n, t, c0, L, ldl, k, theta, D, g)));
     GP_LAUNCH_CHECK();
   }
-  precond_rho<T><<<nb, kThreads, 0, st>>>(n, t, L, ldl, k, theta, D, mode, j, max_iter, g);
+  rho_combine<T><<<1, 256, 0, st>>>(t, nb, mode, j, max_iter, g);
   GP_LAUNCH_CHECK();
   return GP_OK;
 }
@@ -433,6 +541,11 @@ gp_status cg_solve(const Prob& pb, MvmOp& mvm, const T* L, int64_t ldl, int k,
   GP_CUDA_TRY(cudaStreamSynchronize(st));
   *host_status = hs;
   return GP_OK;
+}
+
+size_t cg_atb_part_elems(int64_t n, int k, int t) {
+  (void)n;
+  return (size_t)kLtrBlocks * std::max(k, 1) * std::min(std::max(t, 1), 64);
 }
 
 template <class T>

@@ -23,7 +23,8 @@
 // Roles of a CTA (persistent over (row tile, column chunk) work units):
 //   warp 0      producer: bulk TMA copies (cp.async.bulk) of pre-tiled operand tiles
 //   warp 1      TMEM allocator and single-thread MMA issuer
-//   warps 2-5   epilogue warpgroup (TMEM lanes 32 (w % 4) .. + 31)
+//   warps 2-9   two epilogue warpgroups; warp w reads TMEM lanes 32 (w % 4) .. + 31,
+//               group g = (w - 2) / 4 handles S columns 64 g .. 64 g + 63 of a tile
 // Synchronisation uses mbarriers; every wait gives up after a time limit, sets an
 // abort flag and an error code, and the CTA drains its own copies and MMAs (again
 // with a limit) before freeing TMEM and returning.
@@ -43,7 +44,7 @@ namespace {
 constexpr int BM = 128;        // rows per tile (MMA M)
 constexpr int BN = 128;        // columns per tile (GEMM1 N, GEMM2 K)
 constexpr int kMaxStages = 3;
-constexpr int kThreads = 192;  // 6 warps
+constexpr int kThreads = 320;  // 10 warps
 constexpr long long kWaitNs = 2000000000LL;   // 2 s per wait before giving up
 
 // ---- PTX wrappers -------------------------------------------------------------------
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bars->s_full[b]), 1);
       mbar_init(smem_u32(&bars->s_free[b]), 1);
-      mbar_init(smem_u32(&bars->p_ready[b]), BM);
+      mbar_init(smem_u32(&bars->p_ready[b]), 2 * BM);
     }
     mbar_init(smem_u32(&bars->o_full), 1);
     mbar_init(smem_u32(&bars->o_free), BM);
@@ -382,14 +383,17 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
               if (!first_unit) o_par ^= 1;
             }
             tc_fence_after();
+            // P_hi of K elements 64 g .. 64 g + 63 sits in TMEM columns 64 g .. 64 g + 31
+            // of the S buffer (each epilogue group packs within its own columns)
             const uint32_t v0 = smem_u32(sV + prev_stage * v_bytes);
             for (int kk = 0; kk < BN / 16; ++kk)       // P_hi V_hi
-              mma_ts(t_o, t_s[pbuf] + kk * 8, sdesc(v0 + kk * 256, 128, BN * 16), id2,
-                     (jj > 1 || kk > 0) ? 1u : 0u);
+              mma_ts(t_o, t_s[pbuf] + (kk >> 2) * 64 + (kk & 3) * 8,
+                     sdesc(v0 + kk * 256, 128, BN * 16), id2, (jj > 1 || kk > 0) ? 1u : 0u);
             if (split > 1) {
               const uint32_t v1 = v0 + vh_bytes;
               for (int kk = 0; kk < BN / 16; ++kk)     // P_hi V_lo
-                mma_ts(t_o, t_s[pbuf] + kk * 8, sdesc(v1 + kk * 256, 128, BN * 16), id2, 1u);
+                mma_ts(t_o, t_s[pbuf] + (kk >> 2) * 64 + (kk & 3) * 8,
+                       sdesc(v1 + kk * 256, 128, BN * 16), id2, 1u);
               for (int kk = 0; kk < BN / 16; ++kk)     // P_lo V_hi
                 mma_ts(t_o, t_lo[pbuf] + kk * 8, sdesc(v0 + kk * 256, 128, BN * 16), id2, 1u);
             }
@@ -414,8 +418,9 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
       }
     }
   } else {
-    // ------------------------------------------------------------ epilogue warpgroup
+    // ------------------------------------------------------------ epilogue warpgroups
     const int quarter = warp & 3;                 // TMEM lane quarter of this warp
+    const int group = (warp - 2) >> 2;            // column half of the tile
     const int row = quarter * 32 + lane;          // row within the tile
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const float kscale = (float)g.theta[g.D];
@@ -434,35 +439,39 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         }
         sfull_par[buf] ^= 1;
         tc_fence_after();
-        const uint32_t tb = t_s[buf] + lane_off;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t v[32];
-          GP_TMEM_LD32(tb + c0, v);
-          tmem_wait_ld();
-          if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
-            for (int q = 0; q < 32; ++q) g.dbg[row * BN + c0 + q] = __uint_as_float(v[q]);
-          }
-          uint32_t pk[16], pl[16];
+        const uint32_t tb = t_s[buf] + lane_off + group * 64;
+        uint32_t v[64];
+        GP_TMEM_LD32(tb, v);
+        GP_TMEM_LD32(tb + 32, (v + 32));
+        tmem_wait_ld();
+        if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
+          for (int q = 0; q < 64; ++q) g.dbg[row * BN + group * 64 + q] = __uint_as_float(v[q]);
+        }
+        uint32_t pk[32], pl[32];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const float p0 = kernel_from_s(g.kind, __uint_as_float(v[2 * q]), kscale);
-            const float p1 = kernel_from_s(g.kind, __uint_as_float(v[2 * q + 1]), kscale);
-            const uint32_t h = pack_bf16(p0, p1);
-            pk[q] = h;
-            // residuals of the BF16 rounding, themselves rounded to BF16
-            const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);
-            pl[q] = pack_bf16(p0 - h0, p1 - h1);
-          }
-          GP_TMEM_ST16(tb + (c0 >> 1), pk);
-          if (split > 1) GP_TMEM_ST16(t_lo[buf] + lane_off + (c0 >> 1), pl);
+        for (int q = 0; q < 32; ++q) {
+          const float p0 = kernel_from_s(g.kind, __uint_as_float(v[2 * q]), kscale);
+          const float p1 = kernel_from_s(g.kind, __uint_as_float(v[2 * q + 1]), kscale);
+          const uint32_t h = pack_bf16(p0, p1);
+          pk[q] = h;
+          // residuals of the BF16 rounding, themselves rounded to BF16
+          const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);
+          pl[q] = pack_bf16(p0 - h0, p1 - h1);
+        }
+        GP_TMEM_ST16(tb, pk);
+        GP_TMEM_ST16(tb + 16, (pk + 16));
+        if (split > 1) {
+          const uint32_t tl = t_lo[buf] + lane_off + group * 32;
+          GP_TMEM_ST16(tl, pl);
+          GP_TMEM_ST16(tl + 16, (pl + 16));
         }
         tmem_wait_st();
         tc_fence_before();
         mbar_arrive(smem_u32(&bars->p_ready[buf]));
       }
       if (!ok) break;
-      // the unit's product is complete: O -> partial output
+      if (group != 0) continue;
+      // the unit's product is complete: O -> partial output (first group)
       if (!mbar_wait(smem_u32(&bars->o_full), of_par, abort, g.err, 32)) break;
       of_par ^= 1;
       tc_fence_after();
@@ -478,18 +487,16 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
             if (c0 + q < g.t && grow < g.n) dst[(size_t)(c0 + q) * g.npad + grow] = __uint_as_float(v[q]);
         } else {
           // tp is a multiple of 16: a final half chunk
-          uint32_t w16[32];
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
               "%13,%14,%15}, [%16];"
-              : "=r"(w16[0]), "=r"(w16[1]), "=r"(w16[2]), "=r"(w16[3]), "=r"(w16[4]),
-                "=r"(w16[5]), "=r"(w16[6]), "=r"(w16[7]), "=r"(w16[8]), "=r"(w16[9]),
-                "=r"(w16[10]), "=r"(w16[11]), "=r"(w16[12]), "=r"(w16[13]), "=r"(w16[14]),
-                "=r"(w16[15])
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
               : "r"(t_o + lane_off + c0));
           tmem_wait_ld();
           for (int q = 0; q < 16; ++q)
-            if (c0 + q < g.t && grow < g.n) dst[(size_t)(c0 + q) * g.npad + grow] = __uint_as_float(w16[q]);
+            if (c0 + q < g.t && grow < g.n) dst[(size_t)(c0 + q) * g.npad + grow] = __uint_as_float(v[q]);
         }
       }
       tc_fence_before();

@@ -91,7 +91,7 @@ template <class T>
 struct CgBufs {
   T *X, *R, *Z, *P, *Q;      // n x t, ld n
   T* Sp;                     // k x t: C^-1 L^T R
-  double* atb_part;          // atb_chunks(n) * k * t
+  double* atb_part;          // cg_atb_part_elems(n, k, t): block partials of L^T R
   double* S;                 // k x t
   double* rho;               // t
   double* rho0;              // t
@@ -107,6 +107,7 @@ struct CgBufs {
   unsigned* counter;         // 1
 };
 constexpr int kCgBlocks = 304;
+size_t cg_atb_part_elems(int64_t n, int k, int t);
 // Matrix-vector product used by CG: W = K_hat V on all t columns; `gate` (device
 // int, may be null) lets the product return immediately when it reads 0.
 struct MvmOp {

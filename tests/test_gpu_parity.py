@@ -204,15 +204,18 @@ def test_mbcg_matched(prec, k):
     # run is itself rounding-sensitive, so the check is the property the rule
     # guarantees: the true residual, formed with the (parity-tested) kernel
     # product, is at the tolerance (up to the drift of the recursive residual).
-    res2 = gp.gp_mbcg(prob, torch.from_numpy(L) if k else None, torch.from_numpy(B), o)
+    # FP32 cannot reach 1e-6 on this system (kappa u ~ 3e-4): its run uses 1e-3
+    tol2 = tol if prec == gp.FP64 else 1e-3
+    o2 = gp.opts(cg_tol=tol2, max_iter=max_iter, recompute_every=7)
+    res2 = gp.gp_mbcg(prob, torch.from_numpy(L) if k else None, torch.from_numpy(B), o2)
     it2 = res2["iters"].cpu().numpy()
     if prec == gp.FP64:
         assert np.all(np.abs(it2 - ref["iters"]) <= np.maximum(3, 0.1 * ref["iters"]))
+    assert np.all(it2 < max_iter)
     X2 = res2["X"]
     R = torch.from_numpy(B).to(X2) - gp.gp_kernel_mvm(prob, X2)
     rel = (torch.linalg.norm(R, dim=0) / torch.linalg.norm(torch.from_numpy(B).to(X2), dim=0))
-    # FP32 attains ~kappa u ~ 3e-4 at best on this system
-    assert torch.all(rel <= (5 * tol if prec == gp.FP64 else 1e-3)), rel
+    assert torch.all(rel <= 5 * tol2), rel
 
 
 # ------------------------------------------------------------------ full estimator
