@@ -208,6 +208,42 @@ def run_reference(args, rank, ws, dist):
     _barrier(dist)
 
 
+def run_case(args):
+    """Time one building block on a smaller instance of the workload (same d, kernel,
+    hyperparameters; n points drawn the same way).  Used for profiling captures."""
+    import torch
+    from paper_2107_00243_gb300 import build, gp, workloads
+    build.build()
+    gp.load()
+    prec = {"bf16": gp.BF16, "tf32": gp.TF32, "fp32": gp.FP32}[args.precision]
+    p = workloads.c3_rbf_ard_1e5(n=args.n or 100000, precision=prec)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, prec)
+    t = p.n_probes + 1
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    V = torch.randn(p.n, t, device="cuda", generator=gen)
+    times = []
+    if args.case == "kmvm":
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gp.gp_kernel_mvm(prob, V)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    else:
+        L, piv, rank = gp.gp_pivchol(prob, p.k)
+        o = gp.opts(cg_tol=p.tol, max_iter=4, recompute_every=p.recompute_every, seed=0)
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gp.gp_mbcg(prob, L, V, o)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    print(json.dumps({"case": args.case, "n": p.n, "t": t, "precision": args.precision,
+                      "ms": times}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,7 +254,15 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=1,
                     help="timed steps of the plain FP32 form when --precision is mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg"], default="estimator",
+                    help="kmvm / mbcg: time only the kernel product or a short CG call on a "
+                         "smaller instance of the workload (for profiling)")
+    ap.add_argument("--n", type=int, default=None, help="instance size for --case")
+    ap.add_argument("--reps", type=int, default=3, help="calls for --case")
     args = ap.parse_args()
+    if args.case != "estimator":
+        run_case(args)
+        return
     rank, ws, local, dist = _dist()
     if args.impl == "reference":
         run_reference(args, rank, ws, dist)

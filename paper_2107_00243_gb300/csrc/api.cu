@@ -234,6 +234,26 @@ __global__ void copy_col(int64_t n, const T* src, T* dst) {
   if (a < n) dst[a] = src[a];
 }
 
+// A non-blocking side stream and two events per host thread and device.
+struct SideStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int device = -1;
+  bool ok = false;
+};
+SideStream& side_stream() {
+  static thread_local SideStream ss;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!ss.ok || ss.device != dev) {
+    ss.ok = cudaStreamCreateWithFlags(&ss.stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) == cudaSuccess;
+    ss.device = dev;
+  }
+  return ss;
+}
+
 // ---- gp_mll_and_grad plan -----------------------------------------------------------
 template <class T>
 struct MllPlan {
@@ -325,9 +345,18 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
     GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o, P.cg,
                        P.PinvB, pb.n, &host_status, st));
   }
-  // S8: Lanczos quadrature per probe
+  // S8: Lanczos quadrature per probe.  It needs only the CG coefficients, uses one
+  // block per probe, and runs on a side stream next to S9 and S10.
+  SideStream& side = side_stream();
+  if (!side.ok) {
+    set_error("could not create the side stream");
+    return GP_ERR_CUDA;
+  }
+  GP_CUDA_TRY(cudaEventRecord(side.fork, st));
+  GP_CUDA_TRY(cudaStreamWaitEvent(side.stream, side.fork, 0));
   GP_TRY(lanczos_logquad(nl, 1, o.max_iter, P.cg.alpha, P.cg.beta, P.cg.iters, P.cg.rho0,
-                         out + GP_OUT_GAMMA(pb.p), P.cg.status, st));
+                         out + GP_OUT_GAMMA(pb.p), P.cg.status, side.stream));
+  GP_CUDA_TRY(cudaEventRecord(side.join, side.stream));
   // quadratic term y^T u
   GP_TRY(dot_into<T>(pb.n, y, P.cg.X, P.part, P.counter, out + GP_OUT_QUAD, st));
   // S9: gradient contraction with A = [u, K^-1 z_i], B = [u, P^-1 z_i]
@@ -342,6 +371,7 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
                           P.core.Cinv, P.prec, out + GP_OUT_TRP(pb.p), out + GP_OUT_PROBEP(pb.p),
                           st));
   // S11: assembly
+  GP_CUDA_TRY(cudaStreamWaitEvent(st, side.join, 0));
   assemble<<<1, 32, 0, st>>>(pb.n, pb.p, nl, k, P.rank, P.cg.iters, P.pivots, P.cg.status,
                              nullptr, out, iout);
   GP_LAUNCH_CHECK();

@@ -51,23 +51,32 @@ __global__ void scale_inputs(int64_t n, int d, int ard, const T* __restrict__ X,
   Xs[e] = (T)(((double)X[e] - mean[j]) / l);
 }
 
+// Rows per thread: two for FP32 (halves the shared-memory broadcasts per kernel
+// entry), one for FP64 (register budget).
+template <class T> struct Rpt { static constexpr int v = 2; };
+template <> struct Rpt<double> { static constexpr int v = 1; };
+
 template <class T, int DM, int TC>
 __global__ void __launch_bounds__(kBM) kmvm_kernel(
     int64_t n, int d, int kind, int D, const double* __restrict__ theta,
     const T* __restrict__ Xs, const T* __restrict__ V, int64_t ldv, int tc,
     T* __restrict__ out, int64_t ldo, int64_t split_cols, int add_noise, const int* gate) {
+  constexpr int R = Rpt<T>::v;
   if (gate && *gate == 0) return;
-  __shared__ T sx[kBN][DM];
-  __shared__ T sv[kBN][TC];
+  __shared__ __align__(16) T sx[kBN][DM];
+  __shared__ __align__(16) T sv[kBN][TC];
   const T s = (T)theta[D];
-  const int64_t i = blockIdx.x * (int64_t)kBM + threadIdx.x;
-  T xi[DM];
+  int64_t i[R];
+  T xi[R][DM];
+  T acc[R][TC];
 #pragma unroll
-  for (int q = 0; q < DM; ++q) xi[q] = (i < n && q < d) ? Xs[i * d + q] : T(0);
-  T acc[TC];
+  for (int r = 0; r < R; ++r) {
+    i[r] = blockIdx.x * (int64_t)(kBM * R) + r * kBM + threadIdx.x;
 #pragma unroll
-  for (int c = 0; c < TC; ++c) acc[c] = T(0);
-
+    for (int q = 0; q < DM; ++q) xi[r][q] = (i[r] < n && q < d) ? Xs[i[r] * d + q] : T(0);
+#pragma unroll
+    for (int c = 0; c < TC; ++c) acc[r][c] = T(0);
+  }
   const int64_t jb = blockIdx.y * split_cols;
   const int64_t je = min(n, jb + split_cols);
   for (int64_t j0 = jb; j0 < je; j0 += kBN) {
@@ -82,25 +91,35 @@ __global__ void __launch_bounds__(kBM) kmvm_kernel(
     }
     __syncthreads();
     for (int jj = 0; jj < jn; ++jj) {
-      T r2 = T(0);
+      T kv[R];
 #pragma unroll
-      for (int q = 0; q < DM; ++q) {
-        T df = xi[q] - sx[jj][q];
-        r2 = fma(df, df, r2);
+      for (int r = 0; r < R; ++r) {
+        T r2 = T(0);
+#pragma unroll
+        for (int q = 0; q < DM; ++q) {
+          T df = xi[r][q] - sx[jj][q];
+          r2 = fma(df, df, r2);
+        }
+        kv[r] = kval<T>(kind, r2, s);
       }
-      const T kv = kval<T>(kind, r2, s);
 #pragma unroll
-      for (int c = 0; c < TC; ++c) acc[c] = fma(kv, sv[jj][c], acc[c]);
+      for (int c = 0; c < TC; ++c) {
+        const T v = sv[jj][c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r][c] = fma(kv[r], v, acc[r][c]);
+      }
     }
     __syncthreads();
   }
-  if (i < n) {
-    const T s2 = (T)theta[D + 1];
-    T* o = out + (int64_t)blockIdx.y * tc * ldo;   // split partial (blockIdx.y = 0 if none)
+  const T s2 = (T)theta[D + 1];
+  T* o = out + (int64_t)blockIdx.y * tc * ldo;   // split partial (blockIdx.y = 0 if none)
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (i[r] >= n) continue;
     for (int c = 0; c < tc; ++c) {
-      T v = acc[c];
-      if (add_noise) v = fma(s2, V[i + c * ldv], v);
-      o[i + c * ldo] = v;
+      T v = acc[r][c];
+      if (add_noise) v = fma(s2, V[i[r] + c * ldv], v);
+      o[i[r] + c * ldo] = v;
     }
   }
 }
@@ -313,7 +332,7 @@ __global__ void diag_contract_kernel(int64_t n, const T* __restrict__ A, int64_t
 }
 
 int pick_dm(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32; }
-int pick_tc(int t) { return t <= 8 ? 8 : t <= 16 ? 16 : t <= 32 ? 32 : 64; }
+int pick_tc(int t) { return t <= 8 ? 8 : t <= 16 ? 16 : t <= 32 ? 32 : t <= 48 ? 48 : 64; }
 
 int64_t split_cols_for(int64_t n, int64_t row_blocks, int* splits) {
   // aim for >= ~4 CTAs per SM; each split spans >= 256 columns
@@ -341,10 +360,12 @@ int64_t split_cols_for(int64_t n, int64_t row_blocks, int* splits) {
     case 1608: { constexpr int DM = 16, TC = 8; __VA_ARGS__; } break;              \
     case 1616: { constexpr int DM = 16, TC = 16; __VA_ARGS__; } break;             \
     case 1632: { constexpr int DM = 16, TC = 32; __VA_ARGS__; } break;             \
+    case 1648: { constexpr int DM = 16, TC = 48; __VA_ARGS__; } break;             \
     case 1664: { constexpr int DM = 16, TC = 64; __VA_ARGS__; } break;             \
     case 3208: { constexpr int DM = 32, TC = 8; __VA_ARGS__; } break;              \
     case 3216: { constexpr int DM = 32, TC = 16; __VA_ARGS__; } break;             \
     case 3232: { constexpr int DM = 32, TC = 32; __VA_ARGS__; } break;             \
+    case 3248: { constexpr int DM = 32, TC = 48; __VA_ARGS__; } break;             \
     case 3264: { constexpr int DM = 32, TC = 64; __VA_ARGS__; } break;             \
   }
 
@@ -366,8 +387,10 @@ gp_status prep_inputs(const Prob& pb, const PrepBufs& pr, cudaStream_t st) {
 }
 
 size_t simt_scratch_elems(int64_t n, int t) {
+  // the product with two rows per thread has the fewest row blocks, hence the
+  // most column splits
   int splits;
-  split_cols_for(n, cdiv(n, kBM), &splits);
+  split_cols_for(n, cdiv(n, 2 * kBM), &splits);
   int tc = t < 64 ? t : 64;
   return (size_t)splits * tc * n;
 }
@@ -379,7 +402,7 @@ gp_status kmvm_simt(const Prob& pb, const void* Xs_, const void* V_, int64_t ldv
   const T* V = static_cast<const T*>(V_);
   T* W = static_cast<T*>(W_);
   T* part = static_cast<T*>(scratch);
-  const int64_t rb = cdiv(pb.n, kBM);
+  const int64_t rb = cdiv(pb.n, kBM * Rpt<T>::v);
   int splits;
   const int64_t cols = split_cols_for(pb.n, rb, &splits);
   const int dm = pick_dm(pb.d);
