@@ -196,6 +196,33 @@ const char* gp_status_string(int32_t status);
 /* Detail of the last host-side validation failure on this thread (static storage). */
 const char* gp_last_error_message(void);
 
+/* The kernel-matrix product of gp_kernel_mvm, W = (K + sigma^2 I) V, for callers that
+ * cannot allocate device memory.  Such callers include:
+ *   - code running where cudaMalloc is off limits, e.g. inside someone else's
+ *     graph-capture region;
+ *   - real-time loops with a fixed memory budget;
+ *   - host frameworks that own the allocator and hand the library only its input and
+ *     output buffers.
+ * The paper has no counterpart: this repackages gp_kernel_mvm without a workspace.
+ *
+ * Scratch.  One static device array of 16 MiB + 80 KiB inside this library.  Every
+ * GPU that loads the library holds it until the process exits.  Every call reuses
+ * it and leaves its contents behind, so calls that overlap on the GPU (two streams,
+ * or two host threads) race on it; the caller must serialise them.
+ *
+ * First call.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current.  Make that first call before
+ * any stream capture.
+ *
+ * Limits.  Precision GP_FP32 or GP_FP64, and n * d * sizeof(real) <= 16 MiB (for
+ * example n <= 131072 at d = 32 in FP32).  Larger problems are rejected with
+ * GP_ERR_INVALID_ARG before anything runs.
+ *
+ * Calls no cudaMalloc, cudaFree or allocating library routine.  Otherwise behaves
+ * like gp_kernel_mvm.  Asynchronous.                                               */
+gp_status gp_kernel_mvm_noalloc(const gp_problem* prob, const void* V, int64_t ldv, int32_t t,
+                                void* W, int64_t ldw, gp_stream_t stream);
+
 /* Diagnostic for the tensor-core product (precision GP_BF16): computes W exactly
  * as gp_kernel_mvm does and also copies the FP32 exponent tile S of the first
  * 128 x 128 (row, column) tile pair to S_out (device, 128 x 128 row-major):

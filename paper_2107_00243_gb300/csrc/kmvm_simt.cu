@@ -518,3 +518,33 @@ template gp_status contract_simt<double>(const Prob&, const void*, const void*, 
                                          unsigned*, double*, cudaStream_t);
 
 }  // namespace gp
+
+namespace gp {
+// The same product with the column split turned off, so it needs no scratch for
+// split partials (used by the allocation-free entry point in noalloc.cu).
+template <class T>
+gp_status kmvm_simt_unsplit(const Prob& pb, const void* Xs_, const void* V_, int64_t ldv, int t,
+                            void* W_, int64_t ldw, cudaStream_t st) {
+  const T* Xs = static_cast<const T*>(Xs_);
+  const T* V = static_cast<const T*>(V_);
+  T* W = static_cast<T*>(W_);
+  const int64_t rb = cdiv(pb.n, kBM * Rpt<T>::v);
+  const int64_t cols = cdiv(pb.n, kBN) * kBN;
+  const int dm = pick_dm(pb.d);
+  for (int c0 = 0; c0 < t; c0 += 64) {
+    const int tc = std::min(64, t - c0);
+    const int tcp = pick_tc(tc);
+    dim3 grid((unsigned)rb, 1u);
+    GP_DISPATCH_DM_TC(dm, tcp,
+        (kmvm_kernel<T, DM, TC><<<grid, kBM, 0, st>>>(pb.n, pb.d, pb.kind, pb.D, pb.theta, Xs,
+                                                     V + c0 * ldv, ldv, tc, W + c0 * ldw, ldw,
+                                                     cols, 1, nullptr)));
+    GP_LAUNCH_CHECK();
+  }
+  return GP_OK;
+}
+template gp_status kmvm_simt_unsplit<float>(const Prob&, const void*, const void*, int64_t, int,
+                                            void*, int64_t, cudaStream_t);
+template gp_status kmvm_simt_unsplit<double>(const Prob&, const void*, const void*, int64_t, int,
+                                             void*, int64_t, cudaStream_t);
+}  // namespace gp

@@ -22,6 +22,9 @@ template <class T>
 gp_status kmvm_simt(const Prob& pb, const void* Xs, const void* V, int64_t ldv, int t,
                     void* W, int64_t ldw, void* scratch, const int* gate, cudaStream_t st);
 template <class T>
+gp_status kmvm_simt_unsplit(const Prob& pb, const void* Xs, const void* V, int64_t ldv, int t,
+                            void* W, int64_t ldw, cudaStream_t st);
+template <class T>
 gp_status kdmvm_simt(const Prob& pb, const void* Xs, const void* V, int64_t ldv, int t,
                      void* dW, int64_t ldw, void* scratch, cudaStream_t st);
 // Gradient contraction, hot path of Alg. 2:

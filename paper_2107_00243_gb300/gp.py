@@ -80,6 +80,7 @@ def load():
         "gp_last_error_message": (ctypes.c_char_p, []),
         "gp_rademacher": (i32, [ctypes.c_uint64, i32, i64, i32, vp, vp]),
         "gp_tc_exponent_tile": (i32, [P, vp, i64, i32, vp, i64, vp, vp, sz, vp]),
+        "gp_kernel_mvm_noalloc": (i32, [P, vp, i64, i32, vp, i64, vp]),
         "gp_launch_count": (i64, []),
         "gp_mvm_timing": (None, [i32]),
         "gp_mvm_timing_read": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
@@ -190,6 +191,19 @@ def gp_kernel_mvm(prob, V, workspace=None):
                                                   prob.precision), prob.device)
     _check("gp_kernel_mvm", lib.gp_kernel_mvm(prob.cref(), _ptr(Vc), prob.n, t, _ptr(W), prob.n,
                                               _ptr(ws), ws.numel(), _stream()))
+    return W.t()
+
+
+def gp_kernel_mvm_noalloc(prob, V):
+    """W = (K + sigma^2 I) V through the entry point that allocates nothing (its
+    scratch is a static device array inside the library; FP32 / FP64 only)."""
+    lib = load()
+    Vc = _colmajor(V, prob.dtype, prob.device)
+    t = Vc.shape[0]
+    W = torch.empty_like(Vc)
+    _check("gp_kernel_mvm_noalloc",
+           lib.gp_kernel_mvm_noalloc(prob.cref(), _ptr(Vc), prob.n, t, _ptr(W), prob.n,
+                                     _stream()))
     return W.t()
 
 
