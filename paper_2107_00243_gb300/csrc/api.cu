@@ -114,7 +114,7 @@ void plan_cg(Arena& A, const Prob& pb, int k, int t, int max_iter, CgBufs<T>& c)
   c.bnorm2 = A.take<double>(t);
   c.alpha = A.take<double>((size_t)t * max_iter);
   c.beta = A.take<double>((size_t)t * max_iter);
-  c.part = A.take<double>((size_t)t * kCgBlocks);
+  c.part = A.take<double>(cg_part_elems(pb.n, t));
   c.active = A.take<int>(t);
   c.caps = A.take<int>(t);
   c.iters = A.take<int>(t);
@@ -137,17 +137,19 @@ void plan_core(Arena& A, const Prob& pb, int k, CorePlan& P) {
 }
 
 void plan_prec(Arena& A, const Prob& pb, int k, int nl, PrecBufs& b) {
-  size_t K = std::max(k, 1), kb = K + nl;
-  b.Q = A.take<double>((size_t)(pb.p - 1) * K * kb);
+  size_t K = std::max(k, 1), NL = std::max(nl, 1);
+  b.Q = A.take<double>(K * K + NL * K);
   b.dW = A.take<double>((size_t)(pb.p - 1) * K * K);
   b.Lpi = A.take<double>(K * K);
   b.Lpinv = A.take<double>(K * K);
   b.A1 = A.take<double>(K * K);
   b.B1 = A.take<double>(K * K);
   b.tmp = A.take<double>(K * K);
-  b.LtW = A.take<double>(K * std::max(nl, 1) + 512);
-  b.Cv = A.take<double>(K * std::max(nl, 1));
-  b.part = A.take<double>((size_t)atb_chunks(pb.n) * K * kb);
+  b.LtW = A.take<double>(K * NL + 512);
+  b.Cv = A.take<double>(K * NL + 2 * (kMaxD + 1));
+  b.part = reinterpret_cast<double*>(A.take<char>(2 * (size_t)pb.n * K * elem_size(pb.prec)));
+  b.dkpart = A.take<double>(std::max<size_t>((size_t)atb_chunks(pb.n) * K * NL,
+                                              (size_t)cdiv(pb.n, 256) * 2 * (kMaxD + 1)));
 }
 
 // ---- matrix-vector products used by CG ----------------------------------------------

@@ -101,50 +101,73 @@ __global__ void __launch_bounds__(kThreads) cg_init(int64_t n, int t, int max_it
 }
 
 // ---- preconditioner P^-1 R = sigma^-2 (R - L C^-1 L^T R) ------------------------------
-// (1) S_part[b] = L[chunk b]^T R[chunk b]: thread m of the block owns row m of S and
-//     keeps the TC columns in registers; L and R row tiles are staged in shared memory.
+// Both n-long products are skinny GEMMs streaming L (n x k) once from HBM: tiles of
+// L and of the right-hand sides are staged in shared memory with coalesced loads,
+// and each thread keeps a small register tile of the result.
+
+// (1) S_part[b] = L[rows of part b]^T R[rows of part b] for a 64-pivot slice of S.
+//     Thread (tm, tc) of a 16 x 16 grid owns pivots 4 tm .. 4 tm + 3 and columns
+//     tc, tc + 16, ... (CPT of them).
 constexpr int kLtrRows = 32;
-constexpr int kLtrBlocks = 152;   // one wave; each block reduces ~n/152 rows
+constexpr int kLtrM = 64;
+constexpr int kLtrParts = 76;     // row parts; x (k / 64) slices ~ 2 CTAs per SM
 template <class T, int TC>
 __global__ void __launch_bounds__(kThreads) ltr_partial(int64_t n, int t, const T* __restrict__ L,
                                                        int64_t ldl, int k, Dev<T> g) {
   if (*g.n_active == 0) return;
-  __shared__ T sL[kLtrRows][kThreads];
-  __shared__ __align__(16) T sR[kLtrRows][TC];
-  int64_t r0, r1;
-  row_chunk(n, &r0, &r1);
-  for (int mb = 0; mb < k; mb += kThreads) {
-    const int m = mb + threadIdx.x;
-    T acc[TC];
+  constexpr int CPT = TC / 16;
+  // padded so that the coalesced staging stores and the compute reads both stay
+  // (nearly) free of bank conflicts
+  __shared__ T sL[kLtrM][kLtrRows + 1];
+  __shared__ T sR[kLtrRows][TC + 1];
+  const int tm = threadIdx.x & 15, tcol = threadIdx.x >> 4;
+  const int m0 = blockIdx.x * kLtrM;
+  const int64_t per = (n + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = blockIdx.y * per, r1 = min(n, r0 + per);
+  T acc[4][CPT];
 #pragma unroll
-    for (int c = 0; c < TC; ++c) acc[c] = T(0);
-    for (int64_t rb = r0; rb < r1; rb += kLtrRows) {
-      const int rn = (int)min((int64_t)kLtrRows, r1 - rb);
-      __syncthreads();
-      for (int e = threadIdx.x; e < kLtrRows * kThreads; e += kThreads) {
-        const int rr = e % kLtrRows, mm = e / kLtrRows;
-        sL[rr][mm] = (rr < rn && mb + mm < k) ? L[rb + rr + (int64_t)(mb + mm) * ldl] : T(0);
-      }
-      for (int e = threadIdx.x; e < kLtrRows * TC; e += kThreads) {
-        const int rr = e % kLtrRows, c = e / kLtrRows;
-        sR[rr][c] = (rr < rn && c < t) ? g.R[rb + rr + (int64_t)c * n] : T(0);
-      }
-      __syncthreads();
-#pragma unroll 4
-      for (int rr = 0; rr < kLtrRows; ++rr) {
-        const T l = sL[rr][threadIdx.x];
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < TC; ++c) acc[c] = fma(l, sR[rr][c], acc[c]);
+    for (int c = 0; c < CPT; ++c) acc[a][c] = T(0);
+  for (int64_t rb = r0; rb < r1; rb += kLtrRows) {
+    const int rn = (int)min((int64_t)kLtrRows, r1 - rb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kLtrRows * kLtrM; e += kThreads) {
+      const int rr = e % kLtrRows, mm = e / kLtrRows;     // rows fastest: coalesced
+      sL[mm][rr] = (rr < rn && m0 + mm < k) ? L[rb + rr + (int64_t)(m0 + mm) * ldl] : T(0);
+    }
+    for (int e = threadIdx.x; e < kLtrRows * TC; e += kThreads) {
+      const int rr = e % kLtrRows, c = e / kLtrRows;
+      sR[rr][c] = (rr < rn && c < t) ? g.R[rb + rr + (int64_t)c * n] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kLtrRows; ++rr) {
+      T lv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) lv[a] = sL[tm * 4 + a][rr];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const T rv = sR[rr][tcol + 16 * c];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][c] = fma(lv[a], rv, acc[a][c]);
       }
     }
-    if (m < k) {
-      double* out = g.S + (size_t)blockIdx.x * k * t;   // per-block partials
-      for (int c = 0; c < t; ++c) out[(size_t)m * t + c] = (double)acc[c];
+  }
+  double* out = g.S + (size_t)blockIdx.y * k * t;     // per-part partials (k x t)
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int m = m0 + tm * 4 + a;
+    if (m >= k) continue;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int col = tcol + 16 * c;
+      if (col < t) out[(size_t)m * t + col] = (double)acc[a][c];
     }
   }
 }
 
-// (2) S = sum of the block partials (FP64), Sp = C^-1 S (FP64), for active columns.
+// (2) S = sum of the part partials (FP64), Sp = C^-1 S (FP64), for active columns.
 template <class T>
 __global__ void reduce_cinv(int k, int t, int ldsp, int nparts, const double* __restrict__ Cinv,
                             const double* __restrict__ part, Dev<T> g) {
@@ -171,80 +194,94 @@ __global__ void reduce_cinv(int k, int t, int ldsp, int nparts, const double* __
   g.Sp[(int64_t)i * ldsp + c] = (T)(a0 + a1);
 }
 
-// (3) z = sigma^-2 (r - L Sp) and the partial sums of r^T z for active columns.
-//   mode 0 (start): rho = rho0 = r^T z
-//   mode 1 (step j): beta_j = rho' / rho, rho = rho'
-constexpr int kPm = 64;   // rows of Sp staged per tile
+// (3) z = sigma^-2 (r - L Sp) and the partial sums of r^T z for active columns, one
+//     128-row tile per block.  Thread (tr, tc) of a 32 x 8 grid owns rows
+//     4 tr .. 4 tr + 3 and columns tc, tc + 8, ... (CPT of them).
+constexpr int kPrRows = 128;
+constexpr int kPrM = 32;
 template <class T, int TC>
 __global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, int c0,
                                                        const T* __restrict__ L, int64_t ldl,
                                                        int k, const double* __restrict__ theta,
                                                        int D, Dev<T> g) {
   if (*g.n_active == 0) return;
-  __shared__ __align__(16) T ssp[kPm][TC];
+  constexpr int CPT = TC / 8;
+  __shared__ __align__(16) T sL[kPrM][kPrRows];
+  __shared__ T sSp[kPrM][TC];
   __shared__ double swarp[kThreads / 32][TC];
-  const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tr = threadIdx.x & 31, tcol = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
+  const int64_t a0 = blockIdx.x * (int64_t)kPrRows;
   const int tc = min(TC, t - c0);
   const T inv_s2 = (T)(1.0 / theta[D + 1]);
-  T rz[TC];
+  T acc[4][CPT];
 #pragma unroll
-  for (int c = 0; c < TC; ++c) rz[c] = T(0);
-  for (int64_t a0 = blockIdx.x * (int64_t)kThreads; a0 < n; a0 += (int64_t)nb * kThreads) {
-    const int64_t a = a0 + threadIdx.x;
-    T acc[TC];
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < TC; ++c) acc[c] = T(0);
-    for (int m0 = 0; m0 < k; m0 += kPm) {
-      const int mn = min(kPm, k - m0);
-      __syncthreads();
-      for (int e = threadIdx.x; e < kPm * TC; e += kThreads) {
-        const int mm = e / TC, c = e % TC;
-        ssp[mm][c] = (mm < mn && c < tc) ? g.Sp[(int64_t)(m0 + mm) * t + c0 + c] : T(0);
-      }
-      __syncthreads();
-      if (a < n) {
-        for (int mm = 0; mm < mn; ++mm) {
-          const T l = L[a + (int64_t)(m0 + mm) * ldl];
-#pragma unroll
-          for (int c = 0; c < TC; ++c) acc[c] = fma(l, ssp[mm][c], acc[c]);
-        }
-      }
+    for (int c = 0; c < CPT; ++c) acc[a][c] = T(0);
+  for (int m0 = 0; m0 < k; m0 += kPrM) {
+    const int mn = min(kPrM, k - m0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kPrM * kPrRows; e += kThreads) {
+      const int rr = e % kPrRows, mm = e / kPrRows;      // rows fastest: coalesced
+      const int64_t a = a0 + rr;
+      sL[mm][rr] = (mm < mn && a < n) ? L[a + (int64_t)(m0 + mm) * ldl] : T(0);
     }
-    if (a < n) {
+    for (int e = threadIdx.x; e < kPrM * TC; e += kThreads) {
+      const int mm = e / TC, c = e % TC;
+      sSp[mm][c] = (mm < mn && c < tc) ? g.Sp[(int64_t)(m0 + mm) * t + c0 + c] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int mm = 0; mm < kPrM; ++mm) {
+      T lv[4];
 #pragma unroll
-      for (int c = 0; c < TC; ++c) {
-        if (c < tc && g.active[c0 + c]) {
-          const int64_t off = a + (int64_t)(c0 + c) * n;
-          const T r = g.R[off];
-          const T z = (r - acc[c]) * inv_s2;
-          g.Z[off] = z;
-          rz[c] = fma(r, z, rz[c]);
-        }
+      for (int a = 0; a < 4; ++a) lv[a] = sL[mm][tr * 4 + a];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const T sv = sSp[mm][tcol + 8 * c];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][c] = fma(lv[a], sv, acc[a][c]);
       }
     }
   }
-  // per-column block sums: warp shuffles, then the 8 warp values in order
+  // z, and r^T z summed over this block's rows per column
 #pragma unroll
-  for (int c = 0; c < TC; ++c) {
-    double v = warp_sum((double)rz[c]);
-    if (lane == 0) swarp[warp][c] = v;
+  for (int c = 0; c < CPT; ++c) {
+    const int col = tcol + 8 * c;
+    double rz = 0.0;
+    if (col < tc && g.active[c0 + col]) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int64_t row = a0 + tr * 4 + a;
+        if (row < n) {
+          const int64_t off = row + (int64_t)(c0 + col) * n;
+          const T r = g.R[off];
+          const T z = (r - acc[a][c]) * inv_s2;
+          g.Z[off] = z;
+          rz += (double)r * (double)z;
+        }
+      }
+    }
+    rz = warp_sum(rz);                  // the warp's 32 threads share column col
+    if (tr == 0) swarp[warp][c] = rz;   // warp index == tcol
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < tc; c += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += swarp[w][c];
-    g.part[(c0 + c) * nb + blockIdx.x] = s;
+  const int nb = gridDim.x;
+  for (int col = threadIdx.x; col < tc; col += blockDim.x) {
+    // column col is owned by warp (col % 8), slot (col / 8)
+    g.part[(size_t)(c0 + col) * nb + blockIdx.x] = swarp[col % 8][col / 8];
   }
 }
 
-// Combine the r^T z partials of all column chunks (one small launch).
+// Combine the r^T z partials of all blocks (one small launch).
 template <class T>
 __global__ void rho_combine(int t, int nb, int mode, int j, int max_iter, Dev<T> g) {
   if (*g.n_active == 0) return;
   for (int c = threadIdx.x; c < t; c += blockDim.x) {
     if (!g.active[c]) continue;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += g.part[c * nb + b];
+    for (int b = 0; b < nb; ++b) s += g.part[(size_t)c * nb + b];
     if (mode == 0) {
       g.rho[c] = s;
       g.rho0[c] = s;
@@ -441,11 +478,10 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(int64_t n, const T* a, co
   }
 }
 
-int pick_tc(int t) { return t <= 8 ? 8 : t <= 16 ? 16 : t <= 32 ? 32 : t <= 48 ? 48 : 64; }
+int pick_tc16(int t) { return t <= 16 ? 16 : t <= 32 ? 32 : t <= 48 ? 48 : 64; }
 
 #define GP_TC_DISPATCH(TCv, ...)                        \
   switch (TCv) {                                        \
-    case 8: { constexpr int TC = 8; __VA_ARGS__; } break;   \
     case 16: { constexpr int TC = 16; __VA_ARGS__; } break; \
     case 32: { constexpr int TC = 32; __VA_ARGS__; } break; \
     case 48: { constexpr int TC = 48; __VA_ARGS__; } break; \
@@ -456,33 +492,35 @@ template <class T>
 gp_status precond_apply(int64_t n, int t, const T* L, int64_t ldl, int k, const double* Cinv,
                         const double* theta, int D, int mode, int j, int max_iter,
                         const CgBufs<T>& cb, Dev<T>& g, int nb, cudaStream_t st) {
+  (void)nb;
   if (k > 0) {
     // L^T R, in column chunks of at most 64
-    const int nbl = (int)std::min<int64_t>(kLtrBlocks, cdiv(n, kLtrRows));
     for (int c0 = 0; c0 < t; c0 += 64) {
       const int tc = std::min(64, t - c0);
-      Dev<T> gc = g;                 // this chunk's columns; block partials into atb_part
+      Dev<T> gc = g;                 // this chunk's columns; part partials into atb_part
       gc.R = g.R + (int64_t)c0 * n;
       gc.S = cb.atb_part;
-      GP_TC_DISPATCH(pick_tc(tc),
-                     (ltr_partial<T, TC><<<nbl, kThreads, 0, st>>>(n, tc, L, ldl, k, gc)));
+      dim3 grid((unsigned)cdiv(k, kLtrM), (unsigned)kLtrParts);
+      GP_TC_DISPATCH(pick_tc16(tc),
+                     (ltr_partial<T, TC><<<grid, kThreads, 0, st>>>(n, tc, L, ldl, k, gc)));
       GP_LAUNCH_CHECK();
       Dev<T> gs = g;                 // Sp columns c0.. (leading dimension t)
       gs.active = g.active + c0;
       gs.Sp = g.Sp + c0;
-      dim3 grid((unsigned)cdiv(k, 128), (unsigned)tc);
-      reduce_cinv<T><<<grid, 128, sizeof(double) * k, st>>>(k, tc, t, nbl, Cinv, cb.atb_part,
-                                                           gs);
+      dim3 g2((unsigned)cdiv(k, 128), (unsigned)tc);
+      reduce_cinv<T><<<g2, 128, sizeof(double) * k, st>>>(k, tc, t, kLtrParts, Cinv,
+                                                         cb.atb_part, gs);
       GP_LAUNCH_CHECK();
     }
   }
+  const int nbp = (int)cdiv(n, kPrRows);
   for (int c0 = 0; c0 < t; c0 += 64) {
     const int tc = std::min(64, t - c0);
-    GP_TC_DISPATCH(pick_tc(tc), (precond_rho<T, TC><<<nb, kThreads, 0, st>>>(
-                                    n, t, c0, L, ldl, k, theta, D, g)));
+    GP_TC_DISPATCH(pick_tc16(tc), (precond_rho<T, TC><<<nbp, kThreads, 0, st>>>(
+                                      n, t, c0, L, ldl, k, theta, D, g)));
     GP_LAUNCH_CHECK();
   }
-  rho_combine<T><<<1, 256, 0, st>>>(t, nb, mode, j, max_iter, g);
+  rho_combine<T><<<1, 256, 0, st>>>(t, nbp, mode, j, max_iter, g);
   GP_LAUNCH_CHECK();
   return GP_OK;
 }
@@ -545,7 +583,10 @@ gp_status cg_solve(const Prob& pb, MvmOp& mvm, const T* L, int64_t ldl, int k,
 
 size_t cg_atb_part_elems(int64_t n, int k, int t) {
   (void)n;
-  return (size_t)kLtrBlocks * std::max(k, 1) * std::min(std::max(t, 1), 64);
+  return (size_t)kLtrParts * std::max(k, 1) * std::min(std::max(t, 1), 64);
+}
+size_t cg_part_elems(int64_t n, int t) {
+  return (size_t)std::max<int64_t>(kCgBlocks, cdiv(n, kPrRows)) * std::max(t, 1);
 }
 
 template <class T>

@@ -23,8 +23,8 @@
 // Roles of a CTA (persistent over (row tile, column chunk) work units):
 //   warp 0      producer: bulk TMA copies (cp.async.bulk) of pre-tiled operand tiles
 //   warp 1      TMEM allocator and single-thread MMA issuer
-//   warps 2-9   two epilogue warpgroups; warp w reads TMEM lanes 32 (w % 4) .. + 31,
-//               group g = (w - 2) / 4 handles S columns 64 g .. 64 g + 63 of a tile
+//   warps 2-17  four epilogue warpgroups; warp w reads TMEM lanes 32 (w % 4) .. + 31,
+//               group g = (w - 2) / 4 handles S columns 32 g .. 32 g + 31 of a tile
 // Synchronisation uses mbarriers; every wait gives up after a time limit, sets an
 // abort flag and an error code, and the CTA drains its own copies and MMAs (again
 // with a limit) before freeing TMEM and returning.
@@ -44,8 +44,10 @@ namespace {
 constexpr int BM = 128;        // rows per tile (MMA M)
 constexpr int BN = 128;        // columns per tile (GEMM1 N, GEMM2 K)
 constexpr int kMaxStages = 3;
-constexpr int kThreads = 320;  // 10 warps
-constexpr long long kWaitNs = 2000000000LL;   // 2 s per wait before giving up
+constexpr int kThreads = 576;  // 18 warps
+constexpr long long kWaitNs = 2000000000LL;   // 2 s per drain wait before giving up
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s of SM clock per pipeline wait
+constexpr int kSBuf = 3;       // S / P buffers in TMEM (128 columns each)
 
 // ---- PTX wrappers -------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -79,15 +81,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase with the given parity; false on abort or time-out.
+// Wait for the phase with the given parity; false on abort or time-out.  The limit
+// is checked with the SM cycle counter every 32 polls, so a completed phase is
+// seen within one poll.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
                                           int* err, int code) {
   if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = gtime();
+  const long long t0 = clock64();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (gtime() - t0 > (unsigned long long)kWaitNs) {
+    if (clock64() - t0 > kWaitCycles) {
       *abort = 1;
       atomicExch(err, (int)GP_ERR_DEVICE_TIMEOUT);
       atomicExch(err + 1, code);
@@ -214,7 +219,8 @@ struct TcArgs {
 
 struct __align__(8) Bars {
   unsigned long long full[kMaxStages], empty[kMaxStages];
-  unsigned long long a_full, a_free, s_full[2], s_free[2], p_ready[2], o_full, o_free, drain;
+  unsigned long long a_full, a_free, s_full[kSBuf], s_free[kSBuf], p_ready[kSBuf], o_full, o_free,
+      drain;
   unsigned int tmem_base;
   int abort;
 };
@@ -252,10 +258,10 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
     }
     mbar_init(smem_u32(&bars->a_full), 1);
     mbar_init(smem_u32(&bars->a_free), 1);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kSBuf; ++b) {
       mbar_init(smem_u32(&bars->s_full[b]), 1);
       mbar_init(smem_u32(&bars->s_free[b]), 1);
-      mbar_init(smem_u32(&bars->p_ready[b]), 2 * BM);
+      mbar_init(smem_u32(&bars->p_ready[b]), 4 * BM);
     }
     mbar_init(smem_u32(&bars->o_full), 1);
     mbar_init(smem_u32(&bars->o_free), BM);
@@ -271,11 +277,10 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
-  // TMEM columns: S / P_hi buffers at 0 and 128, O accumulator at 256 (<= 64
-  // columns), P_lo buffers at 320 and 384.
-  const uint32_t t_s[2] = {tmem, tmem + 128};
-  const uint32_t t_o = tmem + 256;
-  const uint32_t t_lo[2] = {tmem + 320, tmem + 384};
+  // TMEM columns: S / P buffers b at 128 b (b < 3), O accumulator at 384 (<= 64
+  // columns).  Epilogue group g packs P_hi of its 32 S columns into its columns
+  // 32 g .. 32 g + 15 and P_lo into 32 g + 16 .. 32 g + 31.
+  const uint32_t t_o = tmem + 384;
   const int nunits = g.ntiles * g.nchunks;
 
   if (warp == 0) {
@@ -332,8 +337,14 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
     if (lane == 0) {
       const uint32_t id1 = idesc_bf16(BM, BN);
       const uint32_t id2 = idesc_bf16(BM, tp);
+      const int nk1 = kx / 16;
+      // descriptors of stage 0; a K-step of 16 elements (256 bytes) adds 16 to the
+      // encoded start address, a stage adds its byte size >> 4
+      const uint64_t dA = sdesc(smem_u32(sA), 128, (uint32_t)kx * 16);
+      const uint64_t dB0 = sdesc(smem_u32(sB), 128, (uint32_t)kx * 16);
+      const uint64_t dV0 = sdesc(smem_u32(sV), 128, BN * 16);
+      const uint64_t b_step = b_bytes >> 4, v_step = v_bytes >> 4, vlo = vh_bytes >> 4;
       uint32_t gtile = 0, a_par = 0, o_par = 0;
-      uint32_t sf_par[2] = {0, 0}, pr_par[2] = {0, 0};
       bool first_unit = true;
       for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
         const int ch = u % g.nchunks;
@@ -343,35 +354,33 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         if (!mbar_wait(smem_u32(&bars->a_full), a_par, abort, g.err, 21)) break;
         a_par ^= 1;
         tc_fence_after();
-        uint32_t prev_stage = 0, prev_buf = 0;
+        uint32_t prev_stage = 0, prev_buf = 0, prev_bph = 0;
         bool ok = true;
         for (int jj = 0; jj <= nt && ok; ++jj) {
           if (jj < nt) {
             const uint32_t st = gtile % nst;
             const uint32_t ph = (gtile / nst) & 1;
-            const uint32_t buf = gtile & 1;
+            const uint32_t buf = gtile % kSBuf, bph = (gtile / kSBuf) & 1;
             if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort, g.err, 22)) { ok = false; break; }
-            if (!mbar_wait(smem_u32(&bars->s_free[buf]), sf_par[buf] ^ 1, abort, g.err, 23)) {
+            if (!mbar_wait(smem_u32(&bars->s_free[buf]), bph ^ 1, abort, g.err, 23)) {
               ok = false;
               break;
             }
-            sf_par[buf] ^= 1;
             tc_fence_after();
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + st * b_bytes);
-            for (int kk = 0; kk < kx / 16; ++kk)
-              mma_ss(t_s[buf], sdesc(a0 + kk * 256, 128, kx * 16), sdesc(b0 + kk * 256, 128, kx * 16),
-                     id1, kk > 0 ? 1u : 0u);
+            const uint64_t db = dB0 + st * b_step;
+            const uint32_t ts = tmem + buf * 128;
+            for (int kk = 0; kk < nk1; ++kk)
+              mma_ss(ts, dA + (uint64_t)kk * 16, db + (uint64_t)kk * 16, id1, kk > 0 ? 1u : 0u);
             mma_commit(smem_u32(&bars->s_full[buf]));
             if (jj == nt - 1) mma_commit(smem_u32(&bars->a_free));
           }
           if (jj > 0) {
             // GEMM2 for the previous tile
             const uint32_t pbuf = prev_buf;
-            if (!mbar_wait(smem_u32(&bars->p_ready[pbuf]), pr_par[pbuf], abort, g.err, 24)) {
+            if (!mbar_wait(smem_u32(&bars->p_ready[pbuf]), prev_bph, abort, g.err, 24)) {
               ok = false;
               break;
             }
-            pr_par[pbuf] ^= 1;
             if (jj == 1) {
               // O is overwritten by this unit's first product: wait until the
               // epilogue has read the previous unit's O
@@ -383,19 +392,24 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
               if (!first_unit) o_par ^= 1;
             }
             tc_fence_after();
-            // P_hi of K elements 64 g .. 64 g + 63 sits in TMEM columns 64 g .. 64 g + 31
-            // of the S buffer (each epilogue group packs within its own columns)
-            const uint32_t v0 = smem_u32(sV + prev_stage * v_bytes);
+            // K elements 32 g .. 32 g + 31: P_hi in TMEM columns 32 g .. + 15, P_lo in
+            // 32 g + 16 .. + 31 of the S buffer (each epilogue group packs in place)
+            const uint64_t dv = dV0 + prev_stage * v_step;
+            const uint32_t ts = tmem + pbuf * 128;
+            const uint32_t acc0 = jj > 1 ? 1u : 0u;
+#pragma unroll
             for (int kk = 0; kk < BN / 16; ++kk)       // P_hi V_hi
-              mma_ts(t_o, t_s[pbuf] + (kk >> 2) * 64 + (kk & 3) * 8,
-                     sdesc(v0 + kk * 256, 128, BN * 16), id2, (jj > 1 || kk > 0) ? 1u : 0u);
+              mma_ts(t_o, ts + (kk >> 1) * 32 + (kk & 1) * 8, dv + (uint64_t)kk * 16, id2,
+                     (kk > 0) ? 1u : acc0);
             if (split > 1) {
-              const uint32_t v1 = v0 + vh_bytes;
+#pragma unroll
               for (int kk = 0; kk < BN / 16; ++kk)     // P_hi V_lo
-                mma_ts(t_o, t_s[pbuf] + (kk >> 2) * 64 + (kk & 3) * 8,
-                       sdesc(v1 + kk * 256, 128, BN * 16), id2, 1u);
+                mma_ts(t_o, ts + (kk >> 1) * 32 + (kk & 1) * 8, dv + vlo + (uint64_t)kk * 16, id2,
+                       1u);
+#pragma unroll
               for (int kk = 0; kk < BN / 16; ++kk)     // P_lo V_hi
-                mma_ts(t_o, t_lo[pbuf] + kk * 8, sdesc(v0 + kk * 256, 128, BN * 16), id2, 1u);
+                mma_ts(t_o, ts + (kk >> 1) * 32 + 16 + (kk & 1) * 8, dv + (uint64_t)kk * 16, id2,
+                       1u);
             }
             mma_commit(smem_u32(&bars->empty[prev_stage]));
             mma_commit(smem_u32(&bars->s_free[pbuf]));
@@ -403,7 +417,8 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
           }
           if (jj < nt) {
             prev_stage = gtile % nst;
-            prev_buf = gtile & 1;
+            prev_buf = gtile % kSBuf;
+            prev_bph = (gtile / kSBuf) & 1;
             ++gtile;
           }
         }
@@ -420,36 +435,33 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   } else {
     // ------------------------------------------------------------ epilogue warpgroups
     const int quarter = warp & 3;                 // TMEM lane quarter of this warp
-    const int group = (warp - 2) >> 2;            // column half of the tile
+    const int group = (warp - 2) >> 2;            // S columns 32 g .. 32 g + 31
     const int row = quarter * 32 + lane;          // row within the tile
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const float kscale = (float)g.theta[g.D];
     uint32_t gtile = 0, of_par = 0;
-    uint32_t sfull_par[2] = {0, 0};
     for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
       const int rt = u / g.nchunks, ch = u % g.nchunks;
       const int j0 = ch * g.tiles_per_chunk;
       const int j1 = min(g.ntiles, j0 + g.tiles_per_chunk);
       bool ok = true;
       for (int j = j0; j < j1; ++j, ++gtile) {
-        const uint32_t buf = gtile & 1;
-        if (!mbar_wait(smem_u32(&bars->s_full[buf]), sfull_par[buf], abort, g.err, 31)) {
+        const uint32_t buf = gtile % kSBuf;
+        if (!mbar_wait(smem_u32(&bars->s_full[buf]), (gtile / kSBuf) & 1, abort, g.err, 31)) {
           ok = false;
           break;
         }
-        sfull_par[buf] ^= 1;
         tc_fence_after();
-        const uint32_t tb = t_s[buf] + lane_off + group * 64;
-        uint32_t v[64];
+        const uint32_t tb = tmem + buf * 128 + lane_off + group * 32;
+        uint32_t v[32];
         GP_TMEM_LD32(tb, v);
-        GP_TMEM_LD32(tb + 32, (v + 32));
         tmem_wait_ld();
         if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
-          for (int q = 0; q < 64; ++q) g.dbg[row * BN + group * 64 + q] = __uint_as_float(v[q]);
+          for (int q = 0; q < 32; ++q) g.dbg[row * BN + group * 32 + q] = __uint_as_float(v[q]);
         }
-        uint32_t pk[32], pl[32];
+        uint32_t pk[16], pl[16];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
+        for (int q = 0; q < 16; ++q) {
           const float p0 = kernel_from_s(g.kind, __uint_as_float(v[2 * q]), kscale);
           const float p1 = kernel_from_s(g.kind, __uint_as_float(v[2 * q + 1]), kscale);
           const uint32_t h = pack_bf16(p0, p1);
@@ -459,12 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
           pl[q] = pack_bf16(p0 - h0, p1 - h1);
         }
         GP_TMEM_ST16(tb, pk);
-        GP_TMEM_ST16(tb + 16, (pk + 16));
-        if (split > 1) {
-          const uint32_t tl = t_lo[buf] + lane_off + group * 32;
-          GP_TMEM_ST16(tl, pl);
-          GP_TMEM_ST16(tl + 16, (pl + 16));
-        }
+        if (split > 1) GP_TMEM_ST16(tb + 16, pl);
         tmem_wait_st();
         tc_fence_before();
         mbar_arrive(smem_u32(&bars->p_ready[buf]));

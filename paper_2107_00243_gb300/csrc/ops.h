@@ -101,7 +101,7 @@ struct CgBufs {
   double* bnorm2;            // t
   double* alpha;             // t x max_iter
   double* beta;              // t x max_iter
-  double* part;              // t * kCgBlocks
+  double* part;              // cg_part_elems(n, t): per-block column partials
   int* active;               // t
   int* caps;                 // t
   int* iters;                // t
@@ -111,6 +111,7 @@ struct CgBufs {
 };
 constexpr int kCgBlocks = 304;
 size_t cg_atb_part_elems(int64_t n, int k, int t);
+size_t cg_part_elems(int64_t n, int t);
 // Matrix-vector product used by CG: W = K_hat V on all t columns; `gate` (device
 // int, may be null) lets the product return immediately when it reads 0.
 struct MvmOp {
@@ -146,16 +147,17 @@ gp_status rademacher_fill(uint64_t seed, int stream_id, int64_t rows, int cols, 
 
 // ---- preconditioner derivative terms (precond.cu) ---------------------------------------
 struct PrecBufs {
-  double* Q;        // (p-1) x k x (k + l): Ddot_q^T [L | W]
+  double* Q;        // k x k + l x k reals in the problem precision (transposed A1, Cv)
   double* dW;       // (p-1) x k x k: dK/dtheta_q at pivot pairs
   double* Lpi;      // k x k
   double* Lpinv;    // k x k
   double* A1;       // k x k
   double* B1;       // k x k
   double* tmp;      // k x k
-  double* LtW;      // k x l
-  double* Cv;       // k x l
-  double* part;     // atb partials: atb_chunks(n) * k * (k + l)
+  double* LtW;      // k x l (+ scratch for ||w||^2)
+  double* Cv;       // k x l (+ 2 (kMaxD + 1) for the E / F sums)
+  double* part;     // 2 n k reals in the problem precision: Z1 = L A1^T, Z2 = W Cv^T
+  double* dkpart;   // max(atb partials of L^T W, per-block E / F partials)
 };
 template <class T>
 gp_status precond_terms(const Prob& pb, const void* Xs, const T* L, int64_t ldl, int k,

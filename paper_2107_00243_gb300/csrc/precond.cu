@@ -12,89 +12,178 @@
 //   w^T dP w = 2 (Ddot^T w) . c - c^T dW c,   c = L_pi^-T L^T w
 // and for the noise (dP/dsigma^2 = I): trP = sigma^-2 (n - k) + tr(C^-1),
 // probeP = (1/l) sum_i ||w_i||^2.
-// The O(n k (k + l)) products Ddot^T [L | W] are formed tile by tile, generating
-// the kernel-derivative tile on the fly; everything k x k is FP64.
+// Only contractions of Q = Ddot^T [L | W] with fixed matrices are needed:
+//   sum(A1 o Q_L)                 = sum_{a,m} Ddot[a, m] Z1[a, m],  Z1 = L A1^T
+//   sum_i Q_W[:, i] . c_i         = sum_{a,m} Ddot[a, m] Z2[a, m],  Z2 = W Cv^T
+// so two tall GEMMs (n x k) and one fused pass over the n x k (point, pivot)
+// pairs, which evaluates every hyperparameter's derivative of the kernel at once,
+// replace p - 1 passes of an n x k x (k + l) product.  Everything k x k is FP64.
 #include "ops.h"
 
 namespace gp {
 namespace {
 
-constexpr int kTile = 32;
-
-// part[ch][m][c] = sum over chunk rows a of Ddot_q[a, m] * Y[a, c],  Y = [L | W].
+// Out (n x ncol, column-major) = Y (n x kk, column-major, ld ldy) Bt (kk x ncol, row-major).
+// 128 x 64 output tile per block; thread (tr, tc) owns rows 4 tr .. + 3 and columns
+// 8 tc .. + 7; Y and Bt are staged in shared memory 32 deep.
 template <class T>
-__global__ void __launch_bounds__(256) dk_atb_partial(
-    int64_t n, int d, int kind, int ard, int D, int q, const double* __restrict__ theta,
-    const T* __restrict__ Xs, const int* __restrict__ piv, int k,
-    const T* __restrict__ L, int64_t ldl, const T* __restrict__ W, int64_t ldw, int nl,
-    double* __restrict__ part) {
-  __shared__ T sa[kTile][kTile + 1];   // [pivot m][row]
-  __shared__ T sb[kTile][kTile + 1];   // [col c][row]
-  __shared__ T xp[kTile][kMaxD];
-  __shared__ int pv[kTile];
-  const int kb = k + nl;
-  const int m0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile;
-  const int64_t r0 = (int64_t)blockIdx.z * kAtbRows;
-  const int64_t r1 = min(n, r0 + kAtbRows);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const T s = (T)theta[D];
-  const bool is_scale = (q == D);
-  const T qscale = is_scale ? (T)(1.0 / theta[D]) : (T)(1.0 / theta[ard ? q : 0]);
-  for (int e = threadIdx.x; e < kTile; e += 256) pv[e] = (m0 + e < k) ? piv[m0 + e] : -1;
-  __syncthreads();
-  for (int e = threadIdx.x; e < kTile * d; e += 256) {
-    int mm = e / d, u = e % d;
-    xp[mm][u] = pv[mm] >= 0 ? Xs[(int64_t)pv[mm] * d + u] : T(0);
-  }
-  T acc[4] = {T(0), T(0), T(0), T(0)};
-  for (int64_t rb = r0; rb < r1; rb += kTile) {
+__global__ void __launch_bounds__(256) gemm_tall(int64_t n, int kk, int ncol,
+                                                 const T* __restrict__ Y, int64_t ldy,
+                                                 const T* __restrict__ Bt, T* __restrict__ Out) {
+  __shared__ __align__(16) T sY[32][128];
+  __shared__ __align__(16) T sB[32][64];
+  const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;
+  const int64_t a0 = blockIdx.x * (int64_t)128;
+  const int c0 = blockIdx.y * 64;
+  T acc[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[a][c] = T(0);
+  for (int j0 = 0; j0 < kk; j0 += 32) {
+    const int jn = min(32, kk - j0);
     __syncthreads();
-    for (int e = threadIdx.x; e < kTile * kTile; e += 256) {
-      int rr = e & 31, cc = e >> 5;
-      int64_t r = rb + rr;
-      // derivative tile entry (row r, pivot m0 + cc)
-      T v = T(0);
-      if (r < r1 && pv[cc] >= 0) {
-        T r2 = T(0), dq = T(0);
-        for (int u = 0; u < d; ++u) {
-          T df = Xs[r * d + u] - xp[cc][u];
-          r2 = fma(df, df, r2);
-          if (ard && u == q) dq = df * df;
-        }
-        T kv, fac;
-        kval_fac<T>(kind, r2, s, kv, fac);
-        v = is_scale ? kv : (ard ? fac * dq : fac * r2);
-        v *= qscale;
-      }
-      sa[cc][rr] = v;
-      T bv = T(0);
-      int c = j0 + cc;
-      if (r < r1 && c < kb) bv = (c < k) ? L[r + (int64_t)c * ldl] : W[r + (int64_t)(c - k) * ldw];
-      sb[cc][rr] = bv;
+    for (int e = threadIdx.x; e < 32 * 128; e += 256) {
+      const int rr = e % 128, jj = e / 128;
+      const int64_t a = a0 + rr;
+      sY[jj][rr] = (jj < jn && a < n) ? Y[a + (int64_t)(j0 + jj) * ldy] : T(0);
+    }
+    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+      const int cc = e % 64, jj = e / 64;
+      sB[jj][cc] = (jj < jn && c0 + cc < ncol) ? Bt[(size_t)(j0 + jj) * ncol + c0 + cc] : T(0);
     }
     __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < kTile; ++rr) {
-      T bv = sb[tx][rr];
+#pragma unroll 4
+    for (int jj = 0; jj < 32; ++jj) {
+      T yv[4], bv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = fma(sa[ty + 8 * u][rr], bv, acc[u]);
+      for (int a = 0; a < 4; ++a) yv[a] = sY[jj][tr * 4 + a];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) bv[c] = sB[jj][tc * 8 + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[a][c] = fma(yv[a], bv[c], acc[a][c]);
     }
   }
-  double* out = part + (int64_t)blockIdx.z * k * kb;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    int m = m0 + ty + 8 * u, c = j0 + tx;
-    if (m < k && c < kb) out[(int64_t)m * kb + c] = (double)acc[u];
+  for (int a = 0; a < 4; ++a) {
+    const int64_t row = a0 + tr * 4 + a;
+    if (row >= n) continue;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int col = c0 + tc * 8 + c;
+      if (col < ncol) Out[row + (int64_t)col * n] = acc[a][c];
+    }
   }
 }
 
-__global__ void sum_chunks_into(int64_t elems, int chunks, const double* __restrict__ part,
-                                double* __restrict__ out) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= elems) return;
-  double s = 0.0;
-  for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * elems + e];
-  out[e] = s;
+// Bt[j][i] = M[i][j] in the problem precision (M row-major rows x cols, FP64).
+template <class T>
+__global__ void transpose_to(int rows, int cols, const double* __restrict__ M,
+                             T* __restrict__ Bt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int i = e / cols, j = e % cols;
+  Bt[(size_t)j * rows + i] = (T)M[e];
+}
+
+// E[q] = sum_{a,m} Ddot_q[a, m] Z1[a, m],  F[q] = sum_{a,m} Ddot_q[a, m] Z2[a, m] for every
+// lengthscale and the output scale, Ddot_q[a, m] = d k(x_a, x_{piv m}) / d theta_q.
+// One thread per point a, pivots staged in shared memory; per-block FP64 partials.
+constexpr int kDkPiv = 64;
+template <class T, int DM>
+__global__ void __launch_bounds__(256) dk_contract(
+    int64_t n, int d, int kind, int ard, int D, const double* __restrict__ theta,
+    const T* __restrict__ Xs, const int* __restrict__ piv, const int* __restrict__ rank,
+    const T* __restrict__ Z1, const T* __restrict__ Z2, double* __restrict__ part) {
+  constexpr int NQ = DM + 1;                    // lengthscales (or 1) + output scale
+  __shared__ T xp[kDkPiv][DM];
+  __shared__ double sred[8][2 * NQ];
+  const int64_t a = blockIdx.x * (int64_t)256 + threadIdx.x;
+  const int r = *rank;
+  const T s = (T)theta[D];
+  T inv_l[DM];
+#pragma unroll
+  for (int u = 0; u < DM; ++u) inv_l[u] = (u < d) ? (T)(1.0 / theta[ard ? u : 0]) : T(0);
+  const T inv_s = (T)(1.0 / theta[D]);
+  T xa[DM];
+#pragma unroll
+  for (int u = 0; u < DM; ++u) xa[u] = (a < n && u < d) ? Xs[a * d + u] : T(0);
+  double e1[NQ], e2[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { e1[q] = 0.0; e2[q] = 0.0; }
+  for (int m0 = 0; m0 < r; m0 += kDkPiv) {
+    const int mn = min(kDkPiv, r - m0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kDkPiv * DM; e += 256) {
+      const int mm = e / DM, u = e % DM;
+      xp[mm][u] = (mm < mn && u < d) ? Xs[(int64_t)piv[m0 + mm] * d + u] : T(0);
+    }
+    __syncthreads();
+    if (a < n) {
+      T f1[NQ], f2[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) { f1[q] = T(0); f2[q] = T(0); }
+      for (int mm = 0; mm < mn; ++mm) {
+        T df2[DM];
+        T r2 = T(0);
+#pragma unroll
+        for (int u = 0; u < DM; ++u) {
+          const T df = xa[u] - xp[mm][u];
+          df2[u] = df * df;
+          r2 += df2[u];
+        }
+        T kv, fac;
+        kval_fac<T>(kind, r2, s, kv, fac);
+        const T z1 = Z1[a + (int64_t)(m0 + mm) * n];
+        const T z2 = Z2[a + (int64_t)(m0 + mm) * n];
+        if (ard) {
+#pragma unroll
+          for (int u = 0; u < DM; ++u) {
+            const T c = fac * df2[u];
+            f1[u] = fma(c, z1, f1[u]);
+            f2[u] = fma(c, z2, f2[u]);
+          }
+        } else {
+          const T c = fac * r2;
+          f1[0] = fma(c, z1, f1[0]);
+          f2[0] = fma(c, z2, f2[0]);
+        }
+        f1[DM] = fma(kv, z1, f1[DM]);
+        f2[DM] = fma(kv, z2, f2[DM]);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        e1[q] += (double)f1[q];
+        e2[q] += (double)f2[q];
+      }
+    }
+  }
+  // scale to the derivative: lengthscale q: / l_q ; output scale: / s
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double sc = (q == DM) ? (double)inv_s : (double)inv_l[q];
+    const double v1 = warp_sum(e1[q] * sc), v2 = warp_sum(e2[q] * sc);
+    if (lane == 0) { sred[warp][q] = v1; sred[warp][NQ + q] = v2; }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * NQ; e += 256) {
+    double acc = 0.0;
+    for (int w = 0; w < 8; ++w) acc += sred[w][e];
+    part[(size_t)blockIdx.x * 2 * NQ + e] = acc;
+  }
+}
+
+// EF[o] = sum over blocks (o < 2 NQ), fixed order.
+__global__ void dk_combine(int nblk, int w, const double* __restrict__ part,
+                           double* __restrict__ EF) {
+  for (int o = threadIdx.x; o < w; o += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * w + o];
+    EF[o] = acc;
+  }
 }
 
 // dW[q][m1][m2] = dK/dtheta_q (x_{piv m1}, x_{piv m2}) for q < p - 1 (FP64).
@@ -151,10 +240,11 @@ __global__ void combine_b1(int64_t elems, const double* __restrict__ tmp,
 }
 
 // One block per hyperparameter q: the FP64 contractions listed at the top.
+// EF holds E[0..NQ) then F[0..NQ) (NQ = DM + 1; entry DM is the output scale).
 __global__ void __launch_bounds__(256) terms_kernel(
-    int k, int nl, int P, int64_t n, const double* __restrict__ theta, int D,
-    const double* __restrict__ Q, const double* __restrict__ dW, const double* __restrict__ A1,
-    const double* __restrict__ B1, const double* __restrict__ Cv, const double* __restrict__ Cinv,
+    int k, int nl, int P, int64_t n, const double* __restrict__ theta, int D, int NQ, int DM,
+    const double* __restrict__ EF, const double* __restrict__ dW, const double* __restrict__ B1,
+    const double* __restrict__ Cv, const double* __restrict__ Cinv,
     const double* __restrict__ wnorm2, double* __restrict__ trP, double* __restrict__ probeP) {
   __shared__ double sh[32];
   const int q = blockIdx.x;
@@ -169,30 +259,24 @@ __global__ void __launch_bounds__(256) terms_kernel(
     }
     return;
   }
-  const int kb = k + nl;
-  const double* Qq = Q + (int64_t)q * k * kb;
+  const int slot = (q == D) ? DM : q;          // E/F index of this hyperparameter
   const double* dWq = dW + (int64_t)q * k * k;
-  double t1 = 0.0, t2 = 0.0;
-  for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) {
-    int i = (int)(e / k), j = (int)(e % k);
-    t1 += A1[e] * Qq[(int64_t)i * kb + j];
-    t2 += B1[e] * dWq[e];
-  }
-  // probe terms: sum_i [2 Q[:, k+i] . c_i - c_i^T dW c_i]
+  double t2 = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) t2 += B1[e] * dWq[e];
+  // probe terms: sum_i c_i^T dW c_i
   double pr = 0.0;
   for (int64_t e = threadIdx.x; e < (int64_t)k * nl; e += blockDim.x) {
     int m1 = (int)(e / nl), i = (int)(e % nl);
     const double c1 = Cv[(int64_t)m1 * nl + i];
     double row = 0.0;
     for (int m2 = 0; m2 < k; ++m2) row += dWq[(int64_t)m1 * k + m2] * Cv[(int64_t)m2 * nl + i];
-    pr += 2.0 * Qq[(int64_t)m1 * kb + k + i] * c1 - c1 * row;
+    pr += c1 * row;
   }
-  double T1 = block_sum(t1, sh);
   double T2 = block_sum(t2, sh);
   double PR = block_sum(pr, sh);
   if (threadIdx.x == 0) {
-    trP[q] = 2.0 * T1 - T2;
-    probeP[q] = nl > 0 ? PR / nl : 0.0;
+    trP[q] = 2.0 * EF[slot] - T2;
+    probeP[q] = nl > 0 ? (2.0 * EF[NQ + slot] - PR) / nl : 0.0;
   }
 }
 
@@ -220,6 +304,8 @@ __global__ void sumsq_kernel(int64_t n, int nl, const T* __restrict__ W, int64_t
 
 }  // namespace
 
+int dm_of(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32; }
+
 template <class T>
 gp_status precond_terms(const Prob& pb, const void* Xs_, const T* L, int64_t ldl, int k,
                         const int* piv, const int* rank, const T* W, int64_t ldw, int nl,
@@ -227,8 +313,8 @@ gp_status precond_terms(const Prob& pb, const void* Xs_, const T* L, int64_t ldl
                         cudaStream_t st) {
   const T* Xs = static_cast<const T*>(Xs_);
   const int P = pb.p;
-  // ||w||^2 summed over probes (noise entry); reuse the tail of b.tmp for the partials
-  double* wn = b.LtW + (int64_t)k * nl;         // 1 double after LtW
+  // ||w||^2 summed over probes (noise entry); scratch after LtW
+  double* wn = b.LtW + (int64_t)k * nl;
   unsigned* ctr = reinterpret_cast<unsigned*>(wn + 1);
   double* spart = wn + 2;
   {
@@ -237,19 +323,10 @@ gp_status precond_terms(const Prob& pb, const void* Xs_, const T* L, int64_t ldl
     sumsq_kernel<T><<<blocks, 256, 0, st>>>(pb.n, nl, W, ldw, spart, ctr, wn);
     GP_LAUNCH_CHECK();
   }
+  const int DM = dm_of(pb.d), NQ = DM + 1;
+  double* EF = b.Cv + (size_t)std::max(k, 1) * std::max(nl, 1);   // 2 NQ doubles
+  GP_CUDA_TRY(cudaMemsetAsync(EF, 0, sizeof(double) * 2 * NQ, st));
   if (k > 0) {
-    const int kb = k + nl;
-    const int64_t ch = atb_chunks(pb.n);
-    for (int q = 0; q < P - 1; ++q) {
-      dim3 grid((unsigned)cdiv(k, kTile), (unsigned)cdiv(kb, kTile), (unsigned)ch);
-      dk_atb_partial<T><<<grid, 256, 0, st>>>(pb.n, pb.d, pb.kind, pb.ard, pb.D, q, pb.theta, Xs,
-                                              piv, k, L, ldl, W, ldw, nl, b.part);
-      GP_LAUNCH_CHECK();
-      const int64_t el = (int64_t)k * kb;
-      sum_chunks_into<<<(unsigned)cdiv(el, 256), 256, 0, st>>>(el, (int)ch, b.part,
-                                                              b.Q + (int64_t)q * el);
-      GP_LAUNCH_CHECK();
-    }
     dw_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 128), 128, 0, st>>>(pb.d, pb.kind, pb.ard, pb.D,
                                                                        pb.theta, Xs, piv, k, b.dW);
     GP_LAUNCH_CHECK();
@@ -262,12 +339,43 @@ gp_status precond_terms(const Prob& pb, const void* Xs_, const T* L, int64_t ldl
     combine_b1<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, b.tmp,
                                                                    pb.theta, pb.D, b.B1);
     GP_LAUNCH_CHECK();
+    T* Bt = reinterpret_cast<T*>(b.Q);                 // k x k then l x k, problem precision
+    T* Z1 = reinterpret_cast<T*>(b.part);              // n x k
+    T* Z2 = Z1 + (size_t)pb.n * k;                     // n x k
+    // Z1 = L A1^T
+    transpose_to<T><<<(unsigned)cdiv(k * k, 256), 256, 0, st>>>(k, k, b.A1, Bt);
+    GP_LAUNCH_CHECK();
+    dim3 gz((unsigned)cdiv(pb.n, 128), (unsigned)cdiv(k, 64));
+    gemm_tall<T><<<gz, 256, 0, st>>>(pb.n, k, k, L, ldl, Bt, Z1);
+    GP_LAUNCH_CHECK();
     if (nl > 0) {
-      GP_TRY(atb<T>(pb.n, L, ldl, k, W, ldw, nl, b.part, b.LtW, st));      // L^T W
-      GP_TRY(gemm64(k, nl, k, b.Lpinv, 1, b.LtW, 0, b.Cv, 1.0, 0.0, st));  // L_pi^-T L^T W
+      GP_TRY(atb<T>(pb.n, L, ldl, k, W, ldw, nl, b.dkpart, b.LtW, st));   // L^T W
+      GP_TRY(gemm64(k, nl, k, b.Lpinv, 1, b.LtW, 0, b.Cv, 1.0, 0.0, st)); // c_i = L_pi^-T L^T w_i
+      // Z2 = W Cv^T
+      T* Bt2 = Bt + (size_t)k * k;
+      transpose_to<T><<<(unsigned)cdiv(k * nl, 256), 256, 0, st>>>(k, nl, b.Cv, Bt2);
+      GP_LAUNCH_CHECK();
+      gemm_tall<T><<<gz, 256, 0, st>>>(pb.n, nl, k, W, ldw, Bt2, Z2);
+      GP_LAUNCH_CHECK();
+    } else {
+      GP_CUDA_TRY(cudaMemsetAsync(Z2, 0, sizeof(T) * (size_t)pb.n * k, st));
     }
+    const int nblk = (int)cdiv(pb.n, 256);
+    switch (DM) {
+      case 4: dk_contract<T, 4><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.kind, pb.ard, pb.D, pb.theta,
+                                                      Xs, piv, rank, Z1, Z2, b.dkpart); break;
+      case 8: dk_contract<T, 8><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.kind, pb.ard, pb.D, pb.theta,
+                                                      Xs, piv, rank, Z1, Z2, b.dkpart); break;
+      case 16: dk_contract<T, 16><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.kind, pb.ard, pb.D, pb.theta,
+                                                        Xs, piv, rank, Z1, Z2, b.dkpart); break;
+      default: dk_contract<T, 32><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.kind, pb.ard, pb.D, pb.theta,
+                                                        Xs, piv, rank, Z1, Z2, b.dkpart); break;
+    }
+    GP_LAUNCH_CHECK();
+    dk_combine<<<1, 128, 0, st>>>(nblk, 2 * NQ, b.dkpart, EF);
+    GP_LAUNCH_CHECK();
   }
-  terms_kernel<<<P, 256, 0, st>>>(k, nl, P, pb.n, pb.theta, pb.D, b.Q, b.dW, b.A1, b.B1, b.Cv,
+  terms_kernel<<<P, 256, 0, st>>>(k, nl, P, pb.n, pb.theta, pb.D, NQ, DM, EF, b.dW, b.B1, b.Cv,
                                   Cinv, wn, trP, probeP);
   GP_LAUNCH_CHECK();
   return GP_OK;
