@@ -77,6 +77,7 @@ void plan_mvm(Arena& A, const Prob& pb, int t, MvmPlan& P) {
     P.tc.xpack = A.take<char>(tc_xpack_bytes(pb.n, pb.d, pb.prec));
     P.tc.norms = A.take<float>((size_t)pb.n);
     P.tc.vpack = A.take<char>(tc_vpack_bytes(pb.n, t, pb.prec));
+    P.tc.vscale = A.take<float>(128);
     P.tc.part = A.take<float>(tc_part_elems(pb.n, t));
     P.tc.err = A.take<int>(4);
   } else {

@@ -3,22 +3,24 @@
 //   softmax normalisation (K is never stored):
 //
 //   GEMM1  S = A_I B_J^T          (128 x 128 per tile, FP32 in TMEM)
-//          A_i = [c x_i, 1, -c |x_i|^2 / 2],  B_j = [x_j, -c |x_j|^2 / 2 + b, 1]
-//          so S_ij = c (x_i . x_j - |x_i|^2/2 - |x_j|^2/2) + b = -c r_ij^2 / 2 + b.
-//          RBF: c = log2(e), b = log2(s)  ->  k_ij = 2^S_ij.
-//          Matern: c = 1, b = 0           ->  r = sqrt(-2 S), k = s poly(r) e^{-a r}.
+//          A_i = [c x_i, 1, -c |x_i|^2 / 2],  B_j = [x_j, -c |x_j|^2 / 2, 1]
+//          so S_ij = c (x_i . x_j - |x_i|^2/2 - |x_j|^2/2) = -c r_ij^2 / 2.
+//          RBF: c = log2(e)  ->  k_ij / s = 2^S_ij.
+//          Matern: c = 1     ->  r = sqrt(-2 S), k / s = poly(r) e^{-a r}.
 //          Each operand is split into BF16 hi + lo parts and the product is formed as
 //          hi.hi + hi.lo + lo.hi, which keeps ~16 significant bits in S despite the
 //          cancellation between the norms and the dot product.
-//   epilogue  P = k(S) in FP32 registers, split into BF16 P_hi (written back over the
-//          same TMEM columns) and P_lo = bf16(P - P_hi) (its own TMEM columns);
+//   epilogue  P = k(S) / s in [0, 1], FP32 in registers, rounded to FP16 (11
+//          significant bits) and written back over the same TMEM columns;
 //          tcgen05.ld / tcgen05.st, one thread per row.
-//   GEMM2  O_I += P_hi V_hi + P_hi V_lo + P_lo V_hi   (A from TMEM, B = the BF16 hi/lo
-//          parts of the V tile in shared memory).  One BF16 pass is not enough for CG:
-//          with |dP|, |dV| ~ 2^-9 relative, p^T K p of a converged direction
-//          (~sigma^2 |p|^2) drowns in the product's error and CG breaks down; the
-//          three-pass split keeps ~2^-16 relative accuracy at three times the GEMM2
-//          tensor work.
+//   GEMM2  O_I += P [V_hi | V_lo]   (A = P from TMEM, B = the FP16 hi and lo parts of
+//          the V tile in shared memory, N = 2 tp).  Each column c of V is scaled by a
+//          power of two 2^e_c that puts max |V_c| in [2^13, 2^14), so both parts stay
+//          in FP16's normal range; W = s 2^-e_c (O_hi + O_lo) + sigma^2 V.
+//          Accuracy: the FP16 rounding of P perturbs K by E with |E_ij| <= 2^-11 K_ij;
+//          for the n = 1e5 RBF workload |E|_2 is a fraction of sigma^2, so CG stays on a
+//          positive-definite operator.  BF16 P (2^-8) is not enough: |E|_2 exceeds
+//          sigma^2 and CG breaks down (p^T K p <= 0).
 //
 // Roles of a CTA (persistent over (row tile, column chunk) work units):
 //   warp 0      producer: bulk TMA copies (cp.async.bulk) of pre-tiled operand tiles
@@ -37,6 +39,7 @@
 #include "ops.h"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace gp {
 namespace {
@@ -126,25 +129,30 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// The MMA and commit wrappers are executed by a whole converged warp with warp-uniform
+// operands; elect.sync picks the one lane (the same lane every time, as the warp is
+// always complete) that issues the instruction.
 __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t acc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "{\n\t.reg .pred p, e;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                        uint32_t acc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "{\n\t.reg .pred p, e;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+          bar)
       : "memory");
 }
 #define GP_TMEM_LD32(taddr, v)                                                                 \
@@ -157,6 +165,14 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
         "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),         \
         "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),         \
         "=r"(v[31])                                                                            \
+      : "r"(taddr))
+#define GP_TMEM_LD16(taddr, v)                                                                 \
+  asm volatile(                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+      "%14,%15}, [%16];"                                                                       \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),   \
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),            \
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])                                                  \
       : "r"(taddr))
 #define GP_TMEM_ST16(taddr, v)                                                                  \
   asm volatile(                                                                                 \
@@ -177,9 +193,9 @@ __device__ __forceinline__ float ex2(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
   uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
 }
 
@@ -197,6 +213,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+// Same with A = B = F16.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // Byte offset of element (row r, k) inside a tile of `kcols` K-elements (bf16).
 __host__ __device__ __forceinline__ uint32_t tile_off(int r, int k, int kcols) {
@@ -206,12 +226,10 @@ __host__ __device__ __forceinline__ uint32_t tile_off(int r, int k, int kcols) {
 struct TcArgs {
   const __nv_bfloat16* xa;   // ntiles tiles of BM x kx (A form)
   const __nv_bfloat16* xb;   // ntiles tiles of BN x kx (B form)
-  const __nv_bfloat16* vp;   // ntiles tiles of tp x BN
+  const __half* vp;          // ntiles tiles of 2 tp x BN (FP16 hi and lo parts)
   float* part;               // nchunks x tp x npad
   int n, npad, ntiles, nchunks, tiles_per_chunk, kx, tp, t, kind, D;
   int nst;                   // pipeline stages (2 or 3)
-  int split;                 // 1: P V in one BF16 pass; 3: hi/lo split, three passes
-  const double* theta;       // device hyperparameters (output scale for Matern)
   const int* gate;
   int* err;                  // err[0] = status, err[1] = where a wait gave up
   float* dbg;                // optional: S of the first tile of unit 0
@@ -225,26 +243,47 @@ struct __align__(8) Bars {
   int abort;
 };
 
-__device__ __forceinline__ float kernel_from_s(int kind, float sv, float s) {
-  if (kind == GP_RBF) return ex2(sv);
-  float r2 = fmaxf(-2.0f * sv, 0.0f);
-  float r = sqrtf(r2);
+// k(r) / s from the exponent tile value S (see the header).
+template <int KIND>
+__device__ __forceinline__ float kernel_from_s(float sv) {
+  if (KIND == GP_RBF) return ex2(sv);
+  const float r2 = fmaxf(-2.0f * sv, 0.0f);
+  const float r = sqrtf(r2);
   const float L2E = 1.4426950408889634f;
-  if (kind == GP_MATERN32) {
-    float ar = 1.7320508075688772f * r;
-    return s * (1.0f + ar) * ex2(-ar * L2E);
+  if (KIND == GP_MATERN32) {
+    const float ar = 1.7320508075688772f * r;
+    return (1.0f + ar) * ex2(-ar * L2E);
   }
-  float ar = 2.23606797749979f * r;
-  return s * (1.0f + ar + 1.6666666666666667f * r2) * ex2(-ar * L2E);
+  const float ar = 2.23606797749979f * r;
+  return (1.0f + ar + 1.6666666666666667f * r2) * ex2(-ar * L2E);
+}
+
+// One epilogue step: this thread's row, 32 S columns at TMEM address tb -> FP16 P in
+// the first 16 of those columns.
+template <int KIND>
+__device__ __forceinline__ void p_from_s(uint32_t tb, float* dbg) {
+  uint32_t v[32];
+  GP_TMEM_LD32(tb, v);
+  tmem_wait_ld();
+  if (dbg) {
+    for (int q = 0; q < 32; ++q) dbg[q] = __uint_as_float(v[q]);
+  }
+  uint32_t pk[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    pk[q] = pack_f16(kernel_from_s<KIND>(__uint_as_float(v[2 * q])),
+                     kernel_from_s<KIND>(__uint_as_float(v[2 * q + 1])));
+  GP_TMEM_ST16(tb, pk);
+  tmem_wait_st();
 }
 
 __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   if (g.gate && *g.gate == 0) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kx = g.kx, tp = g.tp, nst = g.nst, split = g.split;
-  const uint32_t a_bytes = BM * kx * 2, b_bytes = BN * kx * 2, vh_bytes = tp * BN * 2;
-  const uint32_t v_bytes = (split > 1 ? 2u : 1u) * vh_bytes;   // hi (and lo) parts of V
+  const int kx = g.kx, tp = g.tp, nst = g.nst;
+  const uint32_t a_bytes = BM * kx * 2, b_bytes = BN * kx * 2;
+  const uint32_t v_bytes = 2u * tp * BN * 2;   // FP16 hi and lo parts of V
   unsigned char* sA = smem;
   unsigned char* sB = sA + a_bytes;
   unsigned char* sV = sB + nst * b_bytes;
@@ -277,9 +316,9 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
-  // TMEM columns: S / P buffers b at 128 b (b < 3), O accumulator at 384 (<= 64
-  // columns).  Epilogue group g packs P_hi of its 32 S columns into its columns
-  // 32 g .. 32 g + 15 and P_lo into 32 g + 16 .. 32 g + 31.
+  // TMEM columns: S / P buffers b at 128 b (b < 3), O accumulator at 384 (2 tp <= 128
+  // columns).  Epilogue group g packs the FP16 P of its 32 S columns into its columns
+  // 32 g .. 32 g + 15.
   const uint32_t t_o = tmem + 384;
   const int nunits = g.ntiles * g.nchunks;
 
@@ -333,17 +372,18 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer (whole warp;
+    // waits are polled by every lane, instructions issued by one elected lane)
+    {
       const uint32_t id1 = idesc_bf16(BM, BN);
-      const uint32_t id2 = idesc_bf16(BM, tp);
+      const uint32_t id2 = idesc_f16(BM, 2 * tp);   // B = [V_hi; V_lo], N = 2 tp
       const int nk1 = kx / 16;
       // descriptors of stage 0; a K-step of 16 elements (256 bytes) adds 16 to the
       // encoded start address, a stage adds its byte size >> 4
       const uint64_t dA = sdesc(smem_u32(sA), 128, (uint32_t)kx * 16);
       const uint64_t dB0 = sdesc(smem_u32(sB), 128, (uint32_t)kx * 16);
       const uint64_t dV0 = sdesc(smem_u32(sV), 128, BN * 16);
-      const uint64_t b_step = b_bytes >> 4, v_step = v_bytes >> 4, vlo = vh_bytes >> 4;
+      const uint64_t b_step = b_bytes >> 4, v_step = v_bytes >> 4;
       uint32_t gtile = 0, a_par = 0, o_par = 0;
       bool first_unit = true;
       for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
@@ -366,6 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
               ok = false;
               break;
             }
+            __syncwarp();
             tc_fence_after();
             const uint64_t db = dB0 + st * b_step;
             const uint32_t ts = tmem + buf * 128;
@@ -391,26 +432,20 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
               }
               if (!first_unit) o_par ^= 1;
             }
+            __syncwarp();
             tc_fence_after();
-            // K elements 32 g .. 32 g + 31: P_hi in TMEM columns 32 g .. + 15, P_lo in
-            // 32 g + 16 .. + 31 of the S buffer (each epilogue group packs in place)
+            // K elements 32 g .. 32 g + 31: FP16 P in TMEM columns 32 g .. 32 g + 15 of
+            // the S buffer (each epilogue group packs in place)
             const uint64_t dv = dV0 + prev_stage * v_step;
             const uint32_t ts = tmem + pbuf * 128;
             const uint32_t acc0 = jj > 1 ? 1u : 0u;
+            // P [V_hi | V_lo] into O columns [0, tp) and [tp, 2 tp): the hi and lo parts
+            // of the V tile are adjacent 8-row groups, so one descriptor with N = 2 tp
+            // covers both
 #pragma unroll
-            for (int kk = 0; kk < BN / 16; ++kk)       // P_hi V_hi
+            for (int kk = 0; kk < BN / 16; ++kk)
               mma_ts(t_o, ts + (kk >> 1) * 32 + (kk & 1) * 8, dv + (uint64_t)kk * 16, id2,
                      (kk > 0) ? 1u : acc0);
-            if (split > 1) {
-#pragma unroll
-              for (int kk = 0; kk < BN / 16; ++kk)     // P_hi V_lo
-                mma_ts(t_o, ts + (kk >> 1) * 32 + (kk & 1) * 8, dv + vlo + (uint64_t)kk * 16, id2,
-                       1u);
-#pragma unroll
-              for (int kk = 0; kk < BN / 16; ++kk)     // P_lo V_hi
-                mma_ts(t_o, ts + (kk >> 1) * 32 + 16 + (kk & 1) * 8, dv + (uint64_t)kk * 16, id2,
-                       1u);
-            }
             mma_commit(smem_u32(&bars->empty[prev_stage]));
             mma_commit(smem_u32(&bars->s_free[pbuf]));
             if (jj == nt) mma_commit(smem_u32(&bars->o_full));
@@ -425,7 +460,8 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         first_unit = false;
         if (!ok) break;
       }
-      // drain: a final commit completes once every MMA this thread issued is done
+      // drain: a final commit completes once every MMA this warp issued is done
+      __syncwarp();
       mma_commit(smem_u32(&bars->drain));
       const unsigned long long t0 = gtime();
       while (!mbar_try_wait(smem_u32(&bars->drain), 0) &&
@@ -438,7 +474,6 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
     const int group = (warp - 2) >> 2;            // S columns 32 g .. 32 g + 31
     const int row = quarter * 32 + lane;          // row within the tile
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const float kscale = (float)g.theta[g.D];
     uint32_t gtile = 0, of_par = 0;
     for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
       const int rt = u / g.nchunks, ch = u % g.nchunks;
@@ -453,26 +488,12 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         }
         tc_fence_after();
         const uint32_t tb = tmem + buf * 128 + lane_off + group * 32;
-        uint32_t v[32];
-        GP_TMEM_LD32(tb, v);
-        tmem_wait_ld();
-        if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
-          for (int q = 0; q < 32; ++q) g.dbg[row * BN + group * 32 + q] = __uint_as_float(v[q]);
-        }
-        uint32_t pk[16], pl[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float p0 = kernel_from_s(g.kind, __uint_as_float(v[2 * q]), kscale);
-          const float p1 = kernel_from_s(g.kind, __uint_as_float(v[2 * q + 1]), kscale);
-          const uint32_t h = pack_bf16(p0, p1);
-          pk[q] = h;
-          // residuals of the BF16 rounding, themselves rounded to BF16
-          const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);
-          pl[q] = pack_bf16(p0 - h0, p1 - h1);
-        }
-        GP_TMEM_ST16(tb, pk);
-        if (split > 1) GP_TMEM_ST16(tb + 16, pl);
-        tmem_wait_st();
+        float* dbg = (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0)
+                         ? g.dbg + row * BN + group * 32
+                         : nullptr;
+        if (g.kind == GP_RBF) p_from_s<GP_RBF>(tb, dbg);
+        else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(tb, dbg);
+        else p_from_s<GP_MATERN52>(tb, dbg);
         tc_fence_before();
         mbar_arrive(smem_u32(&bars->p_ready[buf]));
       }
@@ -485,25 +506,18 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
       const int grow = rt * BM + row;
       float* dst = g.part + (size_t)ch * tp * g.npad;
 #pragma unroll 1
-      for (int c0 = 0; c0 < tp; c0 += 32) {
-        uint32_t v[32];
-        if (c0 + 32 <= tp) {
-          GP_TMEM_LD32(t_o + lane_off + c0, v);
-          tmem_wait_ld();
-          for (int q = 0; q < 32; ++q)
-            if (c0 + q < g.t && grow < g.n) dst[(size_t)(c0 + q) * g.npad + grow] = __uint_as_float(v[q]);
-        } else {
-          // tp is a multiple of 16: a final half chunk
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-              "%13,%14,%15}, [%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-              : "r"(t_o + lane_off + c0));
-          tmem_wait_ld();
-          for (int q = 0; q < 16; ++q)
-            if (c0 + q < g.t && grow < g.n) dst[(size_t)(c0 + q) * g.npad + grow] = __uint_as_float(v[q]);
+      for (int c0 = 0; c0 < tp; c0 += 16) {
+        // tp is a multiple of 16; O = columns [0, tp) (V_hi) + [tp, 2 tp) (V_lo)
+        uint32_t v[16], w[16];
+        GP_TMEM_LD16(t_o + lane_off + c0, v);
+        GP_TMEM_LD16(t_o + lane_off + tp + c0, w);
+        tmem_wait_ld();
+        if (grow < g.n) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float o = __uint_as_float(v[q]) + __uint_as_float(w[q]);
+            if (c0 + q < g.t) dst[(size_t)(c0 + q) * g.npad + grow] = o;
+          }
         }
       }
       tc_fence_before();
@@ -520,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
 
 // ---- packing kernels ------------------------------------------------------------------
 // Augmented exponent operands, hi/lo split, in the canonical tile layout.
-// A_i = [c x, 1, -c |x|^2/2] ; B_j = [x, -c |x|^2/2 + b, 1]; A' = [A_hi, A_hi, A_lo],
+// A_i = [c x, 1, -c |x|^2/2] ; B_j = [x, -c |x|^2/2, 1]; A' = [A_hi, A_hi, A_lo],
 // B' = [B_hi, B_lo, B_hi], zero padded to kx.
 __global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __restrict__ Xs,
                               int kind, const double* __restrict__ theta, int D,
@@ -529,7 +543,6 @@ __global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __r
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntiles * BM) return;
   const double c = (kind == GP_RBF) ? 1.4426950408889634 : 1.0;
-  const double b = (kind == GP_RBF) ? log2(theta[D]) : 0.0;
   const int L = d + 2;
   double av[kMaxD + 2], bv[kMaxD + 2];
   double nrm = 0.0;
@@ -542,7 +555,7 @@ __global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __r
   }
   av[d] = valid ? 1.0 : 0.0;
   av[d + 1] = valid ? -0.5 * c * nrm : 0.0;
-  bv[d] = valid ? (-0.5 * c * nrm + b) : 0.0;
+  bv[d] = valid ? -0.5 * c * nrm : 0.0;
   bv[d + 1] = valid ? 1.0 : 0.0;
   if (valid) norms[i] = (float)nrm;
   const int tile = i / BM, r = i % BM;
@@ -564,32 +577,62 @@ __global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __r
   }
 }
 
-// V (n x t FP32, column-major) -> tiles of tp x BN BF16 (rows = columns of V).
-__global__ void pack_v_kernel(int n, int ntiles, int t, int tp, int split,
-                              const float* __restrict__ V, int64_t ldv,
-                              __nv_bfloat16* __restrict__ vp, const int* gate) {
+// Power-of-two column scales of V: scale_c = 2^e_c with max_j |V_jc| scale_c in
+// [2^13, 2^14) (1 for an all-zero or non-finite column).  vscale[c] = scale_c,
+// vscale[kMaxT64 + c] = 1 / scale_c.  One block per column.
+constexpr int kMaxT64 = 64;
+__global__ void colscale_kernel(int n, const float* __restrict__ V, int64_t ldv,
+                                float* __restrict__ vscale, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int c = blockIdx.x;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(V[i + (int64_t)c * ldv]));
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      int e = 0;
+      if (m > 0.f && m <= 3.0e38f) {
+        int ex;
+        frexpf(m, &ex);                       // m = f 2^ex, f in [0.5, 1)
+        e = max(-120, min(120, 14 - ex));     // m 2^e in [2^13, 2^14)
+      }
+      vscale[c] = ldexpf(1.0f, e);
+      vscale[kMaxT64 + c] = ldexpf(1.0f, -e);
+    }
+  }
+}
+
+// V (n x t FP32, column-major) -> tiles of 2 tp x BN FP16: rows [0, tp) the hi parts
+// and rows [tp, 2 tp) the lo parts of the scaled columns (rows = columns of V).
+__global__ void pack_v_kernel(int n, int ntiles, int t, int tp, const float* __restrict__ V,
+                              int64_t ldv, const float* __restrict__ vscale,
+                              __half* __restrict__ vp, const int* gate) {
   if (gate && *gate == 0) return;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)ntiles * BN * tp;
   if (e >= total) return;
   const int j = (int)(e % ((int64_t)ntiles * BN));
   const int c = (int)(e / ((int64_t)ntiles * BN));
-  const float v = (j < n && c < t) ? V[j + (int64_t)c * ldv] : 0.f;
+  const float v = (j < n && c < t) ? V[j + (int64_t)c * ldv] * vscale[c] : 0.f;
   const int tile = j / BN, k = j % BN;
   const size_t part = (size_t)tp * BN * 2;
-  unsigned char* tv = reinterpret_cast<unsigned char*>(vp) + (size_t)tile * part * (split > 1 ? 2 : 1);
-  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-  *reinterpret_cast<__nv_bfloat16*>(tv + tile_off(c, k, BN)) = hi;
-  if (split > 1)
-    *reinterpret_cast<__nv_bfloat16*>(tv + part + tile_off(c, k, BN)) =
-        __float2bfloat16_rn(v - __bfloat162float(hi));
+  unsigned char* tv = reinterpret_cast<unsigned char*>(vp) + (size_t)tile * part * 2;
+  const __half hi = __float2half_rn(v);
+  *reinterpret_cast<__half*>(tv + tile_off(c, k, BN)) = hi;
+  *reinterpret_cast<__half*>(tv + part + tile_off(c, k, BN)) = __float2half_rn(v - __half2float(hi));
 }
 
-// W = sum over chunks + sigma^2 V (NaN on a device-side abort).
+// W = s / scale_c * (sum over chunks) + sigma^2 V (NaN on a device-side abort).
 __global__ void tc_reduce_kernel(int n, int npad, int t, int tp, int nchunks,
                                  const float* __restrict__ part,
                                  const float* __restrict__ V, int64_t ldv,
-                                 const double* __restrict__ theta, int D, float* __restrict__ W,
+                                 const double* __restrict__ theta, int D,
+                                 const float* __restrict__ vscale, float* __restrict__ W,
                                  int64_t ldw, const int* gate, const int* err) {
   if (gate && *gate == 0) return;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -597,6 +640,7 @@ __global__ void tc_reduce_kernel(int n, int npad, int t, int tp, int nchunks,
   const int c = (int)(e / n), i = (int)(e % n);
   float acc = 0.f;
   for (int ch = 0; ch < nchunks; ++ch) acc += part[((size_t)ch * tp + c) * npad + i];
+  acc *= (float)theta[D] * vscale[kMaxT64 + c];
   acc = fmaf((float)theta[D + 1], V[i + (int64_t)c * ldv], acc);
   if (*err) acc = __int_as_float(0x7fc00000);
   W[i + (int64_t)c * ldw] = acc;
@@ -622,14 +666,14 @@ int nchunks_for(int ntiles) {
   return std::max(1, std::min(want, maxc));
 }
 constexpr size_t kSmemCap = 200 * 1024;
-size_t smem_bytes(int kx, int tp, int split, int nst) {
-  size_t b = (size_t)BM * kx * 2 + (size_t)nst * BN * kx * 2 +
-             (size_t)nst * tp * BN * 2 * (split > 1 ? 2 : 1) + sizeof(Bars) + 1024;
+size_t smem_bytes(int kx, int tp, int nst) {
+  size_t b = (size_t)BM * kx * 2 + (size_t)nst * BN * kx * 2 + (size_t)nst * tp * BN * 2 * 2 +
+             sizeof(Bars) + 1024;
   // keep one CTA per SM: it owns all 512 TMEM columns
   return std::max<size_t>(b, 120 * 1024);
 }
-int stages_for(int kx, int tp, int split) {
-  return smem_bytes(kx, tp, split, 3) <= kSmemCap ? 3 : 2;
+int stages_for(int kx, int tp) {
+  return smem_bytes(kx, tp, 3) <= kSmemCap ? 3 : 2;
 }
 
 }  // namespace
@@ -674,11 +718,12 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
   const int npad = nt * BM;
   __nv_bfloat16* xa = static_cast<__nv_bfloat16*>(tb.xpack);
   __nv_bfloat16* xb = xa + (size_t)nt * BM * kx;
-  __nv_bfloat16* vp = static_cast<__nv_bfloat16*>(tb.vpack);
+  __half* vp = static_cast<__half*>(tb.vpack);
   int* err = tb.err;
   const int64_t vtotal = (int64_t)nt * BN * tp;
-  const int split = 3;
-  pack_v_kernel<<<(unsigned)cdiv(vtotal, 256), 256, 0, st>>>(n, nt, t, tp, split, V, ldv, vp,
+  colscale_kernel<<<t, 256, 0, st>>>(n, V, ldv, tb.vscale, gate);
+  GP_LAUNCH_CHECK();
+  pack_v_kernel<<<(unsigned)cdiv(vtotal, 256), 256, 0, st>>>(n, nt, t, tp, V, ldv, tb.vscale, vp,
                                                               gate);
   GP_LAUNCH_CHECK();
   TcArgs a;
@@ -696,15 +741,13 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
   a.t = t;
   a.kind = pb.kind;
   a.D = pb.D;
-  a.theta = pb.theta;
-  a.split = split;
-  a.nst = stages_for(kx, tp, split);
+  a.nst = stages_for(kx, tp);
   a.gate = gate;
   a.err = err;
   a.dbg = dbg;
   // the chunk count must not leave an empty chunk
   a.nchunks = (int)cdiv(nt, a.tiles_per_chunk);
-  const size_t sm = smem_bytes(kx, tp, split, a.nst);
+  const size_t sm = smem_bytes(kx, tp, a.nst);
   static bool attr_set = false;
   if (!attr_set) {
     GP_CUDA_TRY(cudaFuncSetAttribute(kmvm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -716,7 +759,7 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
   kmvm_tc_kernel<<<grid, kThreads, sm, st>>>(a);
   GP_LAUNCH_CHECK();
   tc_reduce_kernel<<<(unsigned)cdiv((int64_t)n * t, 256), 256, 0, st>>>(
-      n, npad, t, tp, a.nchunks, tb.part, V, ldv, pb.theta, pb.D, W, ldw, gate, err);
+      n, npad, t, tp, a.nchunks, tb.part, V, ldv, pb.theta, pb.D, tb.vscale, W, ldw, gate, err);
   GP_LAUNCH_CHECK();
   return GP_OK;
 }

@@ -41,6 +41,7 @@ struct TcBufs {
   void* xpack;       // packed hi/lo operand tiles of the scaled inputs
   float* norms;      // n
   void* vpack;       // packed right-hand-side tiles
+  float* vscale;     // 128: power-of-two column scales of V and their inverses
   float* part;       // split partial sums
   int* err;          // 2 ints: device-side status and the wait that gave up
 };
