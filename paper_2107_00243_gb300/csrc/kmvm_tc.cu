@@ -23,10 +23,13 @@
 //          sigma^2 and CG breaks down (p^T K p <= 0).
 //
 // Roles of a CTA (persistent over (row tile, column chunk) work units):
-//   warp 0      producer: bulk TMA copies (cp.async.bulk) of pre-tiled operand tiles
-//   warp 1      TMEM allocator and single-thread MMA issuer
-//   warps 2-17  four epilogue warpgroups; warp w reads TMEM lanes 32 (w % 4) .. + 31,
-//               group g = (w - 2) / 4 handles S columns 32 g .. 32 g + 31 of a tile
+//   warp 0      producer: bulk TMA copies (cp.async.bulk) of the pre-tiled A and B tiles
+//   warp 1      TMEM allocator; issues GEMM1 of every tile
+//   warp 2      issues GEMM2 of every tile (two issuing warps, so the wait / fence /
+//               commit latencies of the two GEMMs overlap instead of adding up)
+//   warps 3-18  four epilogue warpgroups; warp w reads TMEM lanes 32 (w % 4) .. + 31,
+//               group g = (w - 3) / 4 handles S columns 32 g .. 32 g + 31 of a tile
+//   warp 19     producer of the V tiles for GEMM2 (warp 0 loads A and the B tiles)
 // Synchronisation uses mbarriers; every wait gives up after a time limit, sets an
 // abort flag and an error code, and the CTA drains its own copies and MMAs (again
 // with a limit) before freeing TMEM and returning.
@@ -46,11 +49,15 @@ namespace {
 
 constexpr int BM = 128;        // rows per tile (MMA M)
 constexpr int BN = 128;        // columns per tile (GEMM1 N, GEMM2 K)
-constexpr int kMaxStages = 3;
-constexpr int kThreads = 576;  // 18 warps
+constexpr int kMaxStages = 4;   // per operand ring (B tiles for GEMM1, V tiles for GEMM2)
+constexpr int kThreads = 640;  // 20 warps
+constexpr int kEpiWarp0 = 3;   // first epilogue warp (warps 3 .. 18)
+constexpr int kVWarp = 19;     // producer of the V ring
 constexpr long long kWaitNs = 2000000000LL;   // 2 s per drain wait before giving up
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s of SM clock per pipeline wait
-constexpr int kSBuf = 3;       // S / P buffers in TMEM (128 columns each)
+constexpr int kSBuf = 2;       // FP32 S buffers in TMEM (128 columns each)
+constexpr int kPBuf = 2;       // FP16 P buffers in TMEM (64 columns each)
+constexpr int kEpiWarps = 16;
 
 // ---- PTX wrappers -------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -84,16 +91,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase with the given parity; false on abort or time-out.  The limit
-// is checked with the SM cycle counter every 32 polls, so a completed phase is
-// seen within one poll.
+// try_wait with a suspend-time hint: a waiting thread sleeps until the phase
+// completes (or the hint, 1 ms, runs out) instead of spinning, which keeps the
+// issue slots and the shared-memory pipe free for the warps doing work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(1000000u)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity; false on abort or time-out (checked with
+// the SM cycle counter after every suspended poll).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
                                           int* err, int code) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    for (int i = 0; i < 32; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity)) return true;
     if (*abort) return false;
     if (clock64() - t0 > kWaitCycles) {
       *abort = 1;
@@ -229,16 +247,30 @@ struct TcArgs {
   const __half* vp;          // ntiles tiles of 2 tp x BN (FP16 hi and lo parts)
   float* part;               // nchunks x tp x npad
   int n, npad, ntiles, nchunks, tiles_per_chunk, kx, tp, t, kind, D;
-  int nst;                   // pipeline stages (2 or 3)
+  int nsb, nsv;              // shared-memory stages of the B and V rings (2 .. 4)
   const int* gate;
   int* err;                  // err[0] = status, err[1] = where a wait gave up
   float* dbg;                // optional: S of the first tile of unit 0
 };
 
+// Position in a ring of n pipeline slots and the parity of the slot's current
+// phase, advanced without division (integer division by a runtime n costs tens of
+// instructions, which the issuing warps cannot spare).
+struct Ring {
+  uint32_t idx, phase;
+  __device__ __forceinline__ void next(uint32_t n) {
+    if (++idx == n) {
+      idx = 0;
+      phase ^= 1u;
+    }
+  }
+};
+
 struct __align__(8) Bars {
-  unsigned long long full[kMaxStages], empty[kMaxStages];
-  unsigned long long a_full, a_free, s_full[kSBuf], s_free[kSBuf], p_ready[kSBuf], o_full, o_free,
-      drain;
+  unsigned long long fullB[kMaxStages], emptyB[kMaxStages], fullV[kMaxStages], emptyV[kMaxStages];
+  unsigned long long a_full, a_free, s_full[kSBuf], s_free[kSBuf], p_ready[kPBuf], p_free[kPBuf],
+      o_full, o_free,
+      drain1, drain2;
   unsigned int tmem_base;
   int abort;
 };
@@ -258,53 +290,50 @@ __device__ __forceinline__ float kernel_from_s(float sv) {
   return (1.0f + ar + 1.6666666666666667f * r2) * ex2(-ar * L2E);
 }
 
-// One epilogue step: this thread's row, 32 S columns at TMEM address tb -> FP16 P in
-// the first 16 of those columns.
+// P = k(S)/s for this thread's 32 S values, packed as 16 FP16 pairs.
 template <int KIND>
-__device__ __forceinline__ void p_from_s(uint32_t tb, float* dbg) {
-  uint32_t v[32];
-  GP_TMEM_LD32(tb, v);
-  tmem_wait_ld();
-  if (dbg) {
-    for (int q = 0; q < 32; ++q) dbg[q] = __uint_as_float(v[q]);
-  }
-  uint32_t pk[16];
+__device__ __forceinline__ void p_from_s(const uint32_t (&v)[32], uint32_t (&pk)[16]) {
 #pragma unroll
   for (int q = 0; q < 16; ++q)
     pk[q] = pack_f16(kernel_from_s<KIND>(__uint_as_float(v[2 * q])),
                      kernel_from_s<KIND>(__uint_as_float(v[2 * q + 1])));
-  GP_TMEM_ST16(tb, pk);
-  tmem_wait_st();
 }
+
 
 __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   if (g.gate && *g.gate == 0) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kx = g.kx, tp = g.tp, nst = g.nst;
+  const int kx = g.kx, tp = g.tp, nsb = g.nsb, nsv = g.nsv;
   const uint32_t a_bytes = BM * kx * 2, b_bytes = BN * kx * 2;
   const uint32_t v_bytes = 2u * tp * BN * 2;   // FP16 hi and lo parts of V
   unsigned char* sA = smem;
   unsigned char* sB = sA + a_bytes;
-  unsigned char* sV = sB + nst * b_bytes;
-  Bars* bars = reinterpret_cast<Bars*>(sV + nst * v_bytes);
+  unsigned char* sV = sB + nsb * b_bytes;
+  Bars* bars = reinterpret_cast<Bars*>(sV + nsv * v_bytes);
   volatile int* abort = &bars->abort;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < nst; ++s) {
-      mbar_init(smem_u32(&bars->full[s]), 1);
-      mbar_init(smem_u32(&bars->empty[s]), 1);
+    for (int s = 0; s < kMaxStages; ++s) {
+      mbar_init(smem_u32(&bars->fullB[s]), 1);
+      mbar_init(smem_u32(&bars->emptyB[s]), 1);
+      mbar_init(smem_u32(&bars->fullV[s]), 1);
+      mbar_init(smem_u32(&bars->emptyV[s]), 1);
     }
     mbar_init(smem_u32(&bars->a_full), 1);
     mbar_init(smem_u32(&bars->a_free), 1);
     for (int b = 0; b < kSBuf; ++b) {
-      mbar_init(smem_u32(&bars->s_full[b]), 1);
-      mbar_init(smem_u32(&bars->s_free[b]), 1);
-      mbar_init(smem_u32(&bars->p_ready[b]), 4 * BM);
+      mbar_init(smem_u32(&bars->s_full[b]), 1);            // GEMM1 commit
+      mbar_init(smem_u32(&bars->s_free[b]), kEpiWarps);    // each epilogue warp read S
+    }
+    for (int b = 0; b < kPBuf; ++b) {
+      mbar_init(smem_u32(&bars->p_ready[b]), kEpiWarps);   // each epilogue warp wrote P
+      mbar_init(smem_u32(&bars->p_free[b]), 1);            // GEMM2 commit
     }
     mbar_init(smem_u32(&bars->o_full), 1);
     mbar_init(smem_u32(&bars->o_free), BM);
-    mbar_init(smem_u32(&bars->drain), 1);
+    mbar_init(smem_u32(&bars->drain1), 1);
+    mbar_init(smem_u32(&bars->drain2), 1);
     bars->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -316,50 +345,68 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
-  // TMEM columns: S / P buffers b at 128 b (b < 3), O accumulator at 384 (2 tp <= 128
-  // columns).  Epilogue group g packs the FP16 P of its 32 S columns into its columns
-  // 32 g .. 32 g + 15.
+  // TMEM columns: FP32 S buffers b at 128 b (b < 2), FP16 P buffers b at 256 + 64 b
+  // (b < 2; epilogue group g writes columns 16 g .. 16 g + 15, the packed pairs of
+  // its 32 S columns), O accumulator at 384 (2 tp <= 128 columns).  S is released as
+  // soon as the epilogue has read it, P once GEMM2 has consumed it.
   const uint32_t t_o = tmem + 384;
   const int nunits = g.ntiles * g.nchunks;
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
+  if (warp == 0 || warp == kVWarp) {
+    // ------------------------------------------------------------ producers
+    // warp 0: the row tile A of each unit and the B ring (freed by GEMM1);
+    // warp 19: the V ring (freed by GEMM2).  Separate warps, so neither producer's
+    // wait holds up the other, and B tiles are fetched as early as GEMM1 allows.
     if (lane == 0) {
-      uint32_t gtile = 0, a_par = 0, a_arms = 0;
-      int armed[kMaxStages] = {0, 0, 0};
-      uint32_t arm_par[kMaxStages] = {0, 0, 0};
+      const bool is_b = warp == 0;
+      const int ns = is_b ? nsb : nsv;
+      const uint32_t bytes = is_b ? b_bytes : v_bytes;
+      unsigned char* sbase = is_b ? sB : sV;
+      const unsigned char* gsrc = is_b ? reinterpret_cast<const unsigned char*>(g.xb)
+                                       : reinterpret_cast<const unsigned char*>(g.vp);
+      unsigned long long* fullr = is_b ? bars->fullB : bars->fullV;
+      unsigned long long* emptyr = is_b ? bars->emptyB : bars->emptyV;
+      uint32_t a_par = 0, a_arms = 0;
+      Ring sr{0, 0};
+      int armed[kMaxStages] = {0, 0, 0, 0};
+      uint32_t arm_par[kMaxStages] = {0, 0, 0, 0};
       bool first = true;
       for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
         const int rt = u / g.nchunks, ch = u % g.nchunks;
         const int j0 = ch * g.tiles_per_chunk;
         const int j1 = min(g.ntiles, j0 + g.tiles_per_chunk);
-        if (!first && !mbar_wait(smem_u32(&bars->a_free), a_par, abort, g.err, 11)) break;
-        if (!first) a_par ^= 1;
-        first = false;
-        mbar_expect_tx(smem_u32(&bars->a_full), a_bytes);
-        bulk_g2s(smem_u32(sA), reinterpret_cast<const unsigned char*>(g.xa) + (size_t)rt * a_bytes,
-                 a_bytes, smem_u32(&bars->a_full));
-        ++a_arms;
-        for (int j = j0; j < j1; ++j, ++gtile) {
-          const int st = gtile % nst;
-          const uint32_t ph = (gtile / nst) & 1;
-          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort, g.err, 12)) break;
-          const uint32_t fb = smem_u32(&bars->full[st]);
-          mbar_expect_tx(fb, b_bytes + v_bytes);
-          bulk_g2s(smem_u32(sB + st * b_bytes),
-                   reinterpret_cast<const unsigned char*>(g.xb) + (size_t)j * b_bytes, b_bytes, fb);
-          bulk_g2s(smem_u32(sV + st * v_bytes),
-                   reinterpret_cast<const unsigned char*>(g.vp) + (size_t)j * v_bytes, v_bytes, fb);
+        if (is_b) {
+          if (!first && !mbar_wait(smem_u32(&bars->a_free), a_par, abort, g.err, 11)) break;
+          if (!first) a_par ^= 1;
+          first = false;
+          mbar_expect_tx(smem_u32(&bars->a_full), a_bytes);
+          bulk_g2s(smem_u32(sA),
+                   reinterpret_cast<const unsigned char*>(g.xa) + (size_t)rt * a_bytes, a_bytes,
+                   smem_u32(&bars->a_full));
+          ++a_arms;
+        }
+        bool ok = true;
+        for (int j = j0; j < j1; ++j) {
+          const uint32_t st = sr.idx, ph = sr.phase;
+          if (!mbar_wait(smem_u32(&emptyr[st]), ph ^ 1, abort, g.err, 12)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&fullr[st]);
+          mbar_expect_tx(fb, bytes);
+          bulk_g2s(smem_u32(sbase + st * bytes), gsrc + (size_t)j * bytes, bytes, fb);
           armed[st] = 1;
           arm_par[st] = ph;
+          sr.next(ns);
         }
+        if (!ok) break;
       }
       if (*abort) {
         // drain: every copy this thread issued must land before the CTA exits
-        for (int st = 0; st < nst; ++st) {
+        for (int st = 0; st < ns; ++st) {
           if (!armed[st]) continue;
           const unsigned long long t0 = gtime();
-          while (!mbar_try_wait(smem_u32(&bars->full[st]), arm_par[st]) &&
+          while (!mbar_try_wait(smem_u32(&fullr[st]), arm_par[st]) &&
                  gtime() - t0 < (unsigned long long)kWaitNs) {
           }
         }
@@ -372,130 +419,160 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer (whole warp;
-    // waits are polled by every lane, instructions issued by one elected lane)
-    {
-      const uint32_t id1 = idesc_bf16(BM, BN);
-      const uint32_t id2 = idesc_f16(BM, 2 * tp);   // B = [V_hi; V_lo], N = 2 tp
-      const int nk1 = kx / 16;
-      // descriptors of stage 0; a K-step of 16 elements (256 bytes) adds 16 to the
-      // encoded start address, a stage adds its byte size >> 4
-      const uint64_t dA = sdesc(smem_u32(sA), 128, (uint32_t)kx * 16);
-      const uint64_t dB0 = sdesc(smem_u32(sB), 128, (uint32_t)kx * 16);
-      const uint64_t dV0 = sdesc(smem_u32(sV), 128, BN * 16);
-      const uint64_t b_step = b_bytes >> 4, v_step = v_bytes >> 4;
-      uint32_t gtile = 0, a_par = 0, o_par = 0;
-      bool first_unit = true;
-      for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
-        const int ch = u % g.nchunks;
-        const int j0 = ch * g.tiles_per_chunk;
-        const int j1 = min(g.ntiles, j0 + g.tiles_per_chunk);
-        const int nt = j1 - j0;
-        if (!mbar_wait(smem_u32(&bars->a_full), a_par, abort, g.err, 21)) break;
-        a_par ^= 1;
-        tc_fence_after();
-        uint32_t prev_stage = 0, prev_buf = 0, prev_bph = 0;
-        bool ok = true;
-        for (int jj = 0; jj <= nt && ok; ++jj) {
-          if (jj < nt) {
-            const uint32_t st = gtile % nst;
-            const uint32_t ph = (gtile / nst) & 1;
-            const uint32_t buf = gtile % kSBuf, bph = (gtile / kSBuf) & 1;
-            if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort, g.err, 22)) { ok = false; break; }
-            if (!mbar_wait(smem_u32(&bars->s_free[buf]), bph ^ 1, abort, g.err, 23)) {
-              ok = false;
-              break;
-            }
-            __syncwarp();
-            tc_fence_after();
-            const uint64_t db = dB0 + st * b_step;
-            const uint32_t ts = tmem + buf * 128;
-            for (int kk = 0; kk < nk1; ++kk)
-              mma_ss(ts, dA + (uint64_t)kk * 16, db + (uint64_t)kk * 16, id1, kk > 0 ? 1u : 0u);
-            mma_commit(smem_u32(&bars->s_full[buf]));
-            if (jj == nt - 1) mma_commit(smem_u32(&bars->a_free));
-          }
-          if (jj > 0) {
-            // GEMM2 for the previous tile
-            const uint32_t pbuf = prev_buf;
-            if (!mbar_wait(smem_u32(&bars->p_ready[pbuf]), prev_bph, abort, g.err, 24)) {
-              ok = false;
-              break;
-            }
-            if (jj == 1) {
-              // O is overwritten by this unit's first product: wait until the
-              // epilogue has read the previous unit's O
-              if (!first_unit &&
-                  !mbar_wait(smem_u32(&bars->o_free), o_par, abort, g.err, 25)) {
-                ok = false;
-                break;
-              }
-              if (!first_unit) o_par ^= 1;
-            }
-            __syncwarp();
-            tc_fence_after();
-            // K elements 32 g .. 32 g + 31: FP16 P in TMEM columns 32 g .. 32 g + 15 of
-            // the S buffer (each epilogue group packs in place)
-            const uint64_t dv = dV0 + prev_stage * v_step;
-            const uint32_t ts = tmem + pbuf * 128;
-            const uint32_t acc0 = jj > 1 ? 1u : 0u;
-            // P [V_hi | V_lo] into O columns [0, tp) and [tp, 2 tp): the hi and lo parts
-            // of the V tile are adjacent 8-row groups, so one descriptor with N = 2 tp
-            // covers both
-#pragma unroll
-            for (int kk = 0; kk < BN / 16; ++kk)
-              mma_ts(t_o, ts + (kk >> 1) * 32 + (kk & 1) * 8, dv + (uint64_t)kk * 16, id2,
-                     (kk > 0) ? 1u : acc0);
-            mma_commit(smem_u32(&bars->empty[prev_stage]));
-            mma_commit(smem_u32(&bars->s_free[pbuf]));
-            if (jj == nt) mma_commit(smem_u32(&bars->o_full));
-          }
-          if (jj < nt) {
-            prev_stage = gtile % nst;
-            prev_buf = gtile % kSBuf;
-            prev_bph = (gtile / kSBuf) & 1;
-            ++gtile;
-          }
+    // ------------------------------------------------------------ GEMM1 issuer (whole
+    // warp; waits are polled by every lane, MMAs issued by one elected lane)
+    const uint32_t id1 = idesc_bf16(BM, BN);
+    const int nk1 = kx / 16;
+    // descriptors of stage 0; a K-step of 16 elements (256 bytes) adds 16 to the
+    // encoded start address, a stage adds its byte size >> 4
+    const uint64_t dA = sdesc(smem_u32(sA), 128, (uint32_t)kx * 16);
+    const uint64_t dB0 = sdesc(smem_u32(sB), 128, (uint32_t)kx * 16);
+    const uint64_t b_step = b_bytes >> 4;
+    uint32_t a_par = 0;
+    Ring sr{0, 0}, br{0, 0};   // smem stage ring, TMEM S-buffer ring
+    for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
+      const int ch = u % g.nchunks;
+      const int j0 = ch * g.tiles_per_chunk;
+      const int nt = min(g.ntiles, j0 + g.tiles_per_chunk) - j0;
+      if (!mbar_wait(smem_u32(&bars->a_full), a_par, abort, g.err, 21)) break;
+      a_par ^= 1;
+      bool ok = true;
+      for (int jj = 0; jj < nt; ++jj) {
+        const uint32_t st = sr.idx, buf = br.idx;
+        if (!mbar_wait(smem_u32(&bars->fullB[st]), sr.phase, abort, g.err, 22) ||
+            !mbar_wait(smem_u32(&bars->s_free[buf]), br.phase ^ 1, abort, g.err, 23)) {
+          ok = false;
+          break;
         }
-        first_unit = false;
-        if (!ok) break;
+        __syncwarp();
+        tc_fence_after();
+        const uint64_t db = dB0 + st * b_step;
+        const uint32_t ts = tmem + buf * 128;
+        for (int k0 = 0; k0 < nk1; k0 += 4) {   // kx is 64 or 128
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            mma_ss(ts, dA + (uint64_t)(k0 + q) * 16, db + (uint64_t)(k0 + q) * 16, id1,
+                   (k0 + q) > 0 ? 1u : 0u);
+        }
+        mma_commit(smem_u32(&bars->s_full[buf]));
+        mma_commit(smem_u32(&bars->emptyB[st]));
+        if (jj == nt - 1) mma_commit(smem_u32(&bars->a_free));
+        sr.next(nsb);
+        br.next(kSBuf);
       }
-      // drain: a final commit completes once every MMA this warp issued is done
-      __syncwarp();
-      mma_commit(smem_u32(&bars->drain));
-      const unsigned long long t0 = gtime();
-      while (!mbar_try_wait(smem_u32(&bars->drain), 0) &&
-             gtime() - t0 < (unsigned long long)kWaitNs) {
+      if (!ok) break;
+    }
+    // drain: a final commit completes once every MMA this warp issued is done
+    __syncwarp();
+    mma_commit(smem_u32(&bars->drain1));
+    const unsigned long long t0 = gtime();
+    while (!mbar_try_wait(smem_u32(&bars->drain1), 0) &&
+           gtime() - t0 < (unsigned long long)kWaitNs) {
+    }
+  } else if (warp == 2) {
+    // ------------------------------------------------------------ GEMM2 issuer
+    const uint32_t id2 = idesc_f16(BM, 2 * tp);   // B = [V_hi; V_lo], N = 2 tp
+    const uint64_t dV0 = sdesc(smem_u32(sV), 128, BN * 16);
+    const uint64_t v_step = v_bytes >> 4;
+    uint32_t o_par = 0;
+    Ring sr{0, 0}, br{0, 0};
+    bool first_unit = true;
+    for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
+      const int ch = u % g.nchunks;
+      const int j0 = ch * g.tiles_per_chunk;
+      const int nt = min(g.ntiles, j0 + g.tiles_per_chunk) - j0;
+      bool ok = true;
+      for (int jj = 0; jj < nt; ++jj) {
+        const uint32_t st = sr.idx, buf = br.idx;   // br: ring of P buffers here
+        if (!mbar_wait(smem_u32(&bars->fullV[st]), sr.phase, abort, g.err, 26) ||
+            !mbar_wait(smem_u32(&bars->p_ready[buf]), br.phase, abort, g.err, 24)) {
+          ok = false;
+          break;
+        }
+        // O is overwritten by this unit's first product: wait until the epilogue
+        // has read the previous unit's O
+        if (jj == 0 && !first_unit) {
+          if (!mbar_wait(smem_u32(&bars->o_free), o_par, abort, g.err, 25)) {
+            ok = false;
+            break;
+          }
+          o_par ^= 1;
+        }
+        __syncwarp();
+        tc_fence_after();
+        // K elements 16 kk .. 16 kk + 15: FP16 P in TMEM columns 8 kk .. 8 kk + 7 of the
+        // P buffer.  P [V_hi | V_lo] goes into O columns [0, tp) and [tp, 2 tp): the hi
+        // and lo parts of the V tile are adjacent 8-row groups, so one descriptor with
+        // N = 2 tp covers both.
+        const uint64_t dv = dV0 + st * v_step;
+        const uint32_t tpb = tmem + 256 + buf * 64;
+        const uint32_t acc0 = jj > 0 ? 1u : 0u;
+#pragma unroll
+        for (int kk = 0; kk < BN / 16; ++kk)
+          mma_ts(t_o, tpb + kk * 8, dv + (uint64_t)kk * 16, id2, (kk > 0) ? 1u : acc0);
+        mma_commit(smem_u32(&bars->emptyV[st]));
+        mma_commit(smem_u32(&bars->p_free[buf]));
+        if (jj == nt - 1) mma_commit(smem_u32(&bars->o_full));
+        sr.next(nsv);
+        br.next(kPBuf);
       }
+      first_unit = false;
+      if (!ok) break;
+    }
+    __syncwarp();
+    mma_commit(smem_u32(&bars->drain2));
+    const unsigned long long t0 = gtime();
+    while (!mbar_try_wait(smem_u32(&bars->drain2), 0) &&
+           gtime() - t0 < (unsigned long long)kWaitNs) {
     }
   } else {
     // ------------------------------------------------------------ epilogue warpgroups
+    // (warps kEpiWarp0 .. kEpiWarp0 + 15)
     const int quarter = warp & 3;                 // TMEM lane quarter of this warp
-    const int group = (warp - 2) >> 2;            // S columns 32 g .. 32 g + 31
+    const int group = (warp - kEpiWarp0) >> 2;    // S columns 32 g .. 32 g + 31
     const int row = quarter * 32 + lane;          // row within the tile
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    uint32_t gtile = 0, of_par = 0;
+    uint32_t of_par = 0;
+    Ring br{0, 0}, pr{0, 0};   // S-buffer ring, P-buffer ring
     for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
       const int rt = u / g.nchunks, ch = u % g.nchunks;
       const int j0 = ch * g.tiles_per_chunk;
       const int j1 = min(g.ntiles, j0 + g.tiles_per_chunk);
       bool ok = true;
-      for (int j = j0; j < j1; ++j, ++gtile) {
-        const uint32_t buf = gtile % kSBuf;
-        if (!mbar_wait(smem_u32(&bars->s_full[buf]), (gtile / kSBuf) & 1, abort, g.err, 31)) {
+      for (int j = j0; j < j1; ++j) {
+        const uint32_t buf = br.idx;
+        if (!mbar_wait(smem_u32(&bars->s_full[buf]), br.phase, abort, g.err, 31)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t tb = tmem + buf * 128 + lane_off + group * 32;
-        float* dbg = (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0)
-                         ? g.dbg + row * BN + group * 32
-                         : nullptr;
-        if (g.kind == GP_RBF) p_from_s<GP_RBF>(tb, dbg);
-        else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(tb, dbg);
-        else p_from_s<GP_MATERN52>(tb, dbg);
+        uint32_t v[32];
+        GP_TMEM_LD32(tmem + buf * 128 + lane_off + group * 32, v);
+        tmem_wait_ld();
+        // S is in registers: release the buffer for the next GEMM1
         tc_fence_before();
-        mbar_arrive(smem_u32(&bars->p_ready[buf]));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->s_free[buf]));
+        if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
+          for (int q = 0; q < 32; ++q) g.dbg[row * BN + group * 32 + q] = __uint_as_float(v[q]);
+        }
+        uint32_t pk[16];
+        if (g.kind == GP_RBF) p_from_s<GP_RBF>(v, pk);
+        else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v, pk);
+        else p_from_s<GP_MATERN52>(v, pk);
+        // the P buffer is free once the GEMM2 that read it two tiles ago has completed
+        if (!mbar_wait(smem_u32(&bars->p_free[pr.idx]), pr.phase ^ 1, abort, g.err, 33)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        GP_TMEM_ST16(tmem + 256 + pr.idx * 64 + lane_off + group * 16, pk);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->p_ready[pr.idx]));
+        br.next(kSBuf);
+        pr.next(kPBuf);
       }
       if (!ok) break;
       if (group != 0) continue;
@@ -665,15 +742,24 @@ int nchunks_for(int ntiles) {
   int maxc = std::max(1, ntiles / 16);
   return std::max(1, std::min(want, maxc));
 }
-constexpr size_t kSmemCap = 200 * 1024;
-size_t smem_bytes(int kx, int tp, int nst) {
-  size_t b = (size_t)BM * kx * 2 + (size_t)nst * BN * kx * 2 + (size_t)nst * tp * BN * 2 * 2 +
+constexpr size_t kSmemCap = 220 * 1024;
+size_t smem_bytes(int kx, int tp, int nsb, int nsv) {
+  size_t b = (size_t)BM * kx * 2 + (size_t)nsb * BN * kx * 2 + (size_t)nsv * tp * BN * 2 * 2 +
              sizeof(Bars) + 1024;
   // keep one CTA per SM: it owns all 512 TMEM columns
   return std::max<size_t>(b, 120 * 1024);
 }
-int stages_for(int kx, int tp) {
-  return smem_bytes(kx, tp, 3) <= kSmemCap ? 3 : 2;
+// Deepest B and V rings (2 .. 4 stages each, V first) that fit the shared-memory cap.
+void stages_for(int kx, int tp, int* nsb, int* nsv) {
+  for (int total = 2 * kMaxStages; total >= 4; --total)
+    for (int v = std::min(kMaxStages, total - 2); v >= 2 && total - v <= kMaxStages; --v)
+      if (smem_bytes(kx, tp, total - v, v) <= kSmemCap) {
+        *nsb = total - v;
+        *nsv = v;
+        return;
+      }
+  *nsb = 2;
+  *nsv = 2;
 }
 
 }  // namespace
@@ -741,13 +827,13 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
   a.t = t;
   a.kind = pb.kind;
   a.D = pb.D;
-  a.nst = stages_for(kx, tp);
+  stages_for(kx, tp, &a.nsb, &a.nsv);
   a.gate = gate;
   a.err = err;
   a.dbg = dbg;
   // the chunk count must not leave an empty chunk
   a.nchunks = (int)cdiv(nt, a.tiles_per_chunk);
-  const size_t sm = smem_bytes(kx, tp, a.nst);
+  const size_t sm = smem_bytes(kx, tp, a.nsb, a.nsv);
   static bool attr_set = false;
   if (!attr_set) {
     GP_CUDA_TRY(cudaFuncSetAttribute(kmvm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
