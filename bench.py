@@ -45,14 +45,23 @@ def _peaks():
 
 
 def _traffic_from_profiles(kernel_tag):
-    """Per-launch DRAM bytes recorded from an ncu capture (profiles/*traffic*.txt)."""
+    """Per-launch DRAM bytes of a kernel from an ncu capture (profiles/dram_traffic.txt:
+    tag, bytes, source file, sha256[:16] of that file when the counters were taken).
+    None when there is no entry or the source has changed since."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         for line in f:
             parts = line.split()
-            if len(parts) >= 2 and parts[0] == kernel_tag:
+            if len(parts) >= 4 and parts[0] == kernel_tag:
+                src = os.path.join(ROOT, parts[2])
+                if not os.path.exists(src):
+                    return None
+                with open(src, "rb") as g:
+                    if hashlib.sha256(g.read()).hexdigest()[:16] != parts[3]:
+                        return None
                 try:
                     return float(parts[1])
                 except ValueError:
@@ -333,6 +342,7 @@ def main():
 
     # the plain FP32 form of the same evaluation (speedup denominator of the mixed path)
     fp32_value = None
+    fp32_mll = None
     if prec != gp.FP32 and args.fp32_steps > 0:
         prob32, wsp32, out32, iout32, y32 = setup(gp.FP32)
         # one warm-up evaluation: the plain FP32 form runs for tens of seconds
@@ -340,6 +350,7 @@ def main():
                            iout=iout32)
         tot32, _, _, _ = timed_steps(prob32, wsp32, out32, iout32, y32, args.fp32_steps)
         fp32_value = _max_over_ranks(tot32, dist) / (args.fp32_steps * ws)
+        fp32_mll = gp.unpack(out32, iout32, prob32.p, p.n_probes, p.k)["mll"]
         del wsp32, out32, iout32
 
     # end to end: host (pinned) inputs -> device -> estimator -> host outputs
@@ -418,6 +429,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single"},
         "fp32_form_s_per_eval": fp32_value,
         "speedup_vs_fp32_form": (fp32_value / value) if fp32_value else None,
+        "fp32_form_mll": fp32_mll,
         "iters": res["iters"].tolist(), "mll": res["mll"], "status": res["status"],
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": h2d,
