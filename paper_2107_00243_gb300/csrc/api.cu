@@ -77,9 +77,9 @@ void plan_mvm(Arena& A, const Prob& pb, int t, MvmPlan& P) {
     P.tc.xpack = A.take<char>(tc_xpack_bytes(pb.n, pb.d, pb.prec));
     P.tc.norms = A.take<float>((size_t)pb.n);
     P.tc.vpack = A.take<char>(tc_vpack_bytes(pb.n, t, pb.prec));
-    P.tc.vscale = A.take<float>(128);
+    P.tc.vscale = A.take<float>(kTcVscaleElems);
     P.tc.part = A.take<float>(tc_part_elems(pb.n, t));
-    P.tc.err = A.take<int>(4);
+    P.tc.err = A.take<int>(kTcErrInts);
   } else {
     P.scratch = A.take<char>(elem_size(pb.prec) * simt_scratch_elems(pb.n, t));
   }
@@ -186,7 +186,7 @@ gp_status run_kernel_mvm(const Prob& pb, const void* V, int64_t ldv, int t, void
                          MvmPlan& P, cudaStream_t st) {
   GP_TRY(run_prep<T>(pb, P.prep, st));
   if (P.use_tc) {
-    GP_CUDA_TRY(cudaMemsetAsync(P.tc.err, 0, 4 * sizeof(int), st));
+    GP_CUDA_TRY(cudaMemsetAsync(P.tc.err, 0, kTcErrInts * sizeof(int), st));
     GP_TRY(tc_prepare_inputs(pb, P.prep.pr.Xs, P.tc, st));
     TcMvm op;
     op.pb = pb;
@@ -333,7 +333,7 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   // S5-S7: mBCG
   int host_status = 0;
   if (P.mvm.use_tc) {
-    GP_CUDA_TRY(cudaMemsetAsync(P.mvm.tc.err, 0, 4 * sizeof(int), st));
+    GP_CUDA_TRY(cudaMemsetAsync(P.mvm.tc.err, 0, kTcErrInts * sizeof(int), st));
     GP_TRY(tc_prepare_inputs(pb, Xs, P.mvm.tc, st));
     TcMvm op;
     op.pb = pb;
@@ -608,7 +608,7 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
                        cb.status, st));
   int host_status = 0;
   if (mp.use_tc) {
-    GP_CUDA_TRY(cudaMemsetAsync(mp.tc.err, 0, 4 * sizeof(int), st));
+    GP_CUDA_TRY(cudaMemsetAsync(mp.tc.err, 0, kTcErrInts * sizeof(int), st));
     GP_TRY(tc_prepare_inputs(pb, mp.prep.pr.Xs, mp.tc, st));
     TcMvm op;
     op.pb = pb;
@@ -788,7 +788,7 @@ extern "C" gp_status gp_tc_exponent_tile(const gp_problem* prob, const void* V, 
   plan_mvm(A, pb, t, P);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   GP_TRY(run_prep<float>(pb, P.prep, st));
-  GP_CUDA_TRY(cudaMemsetAsync(P.tc.err, 0, 4 * sizeof(int), st));
+  GP_CUDA_TRY(cudaMemsetAsync(P.tc.err, 0, kTcErrInts * sizeof(int), st));
   GP_TRY(tc_prepare_inputs(pb, P.prep.pr.Xs, P.tc, st));
   return kmvm_tc_debug(pb, P.tc, static_cast<const float*>(V), ldv, t, static_cast<float*>(W),
                        ldw, nullptr, S_out, st);

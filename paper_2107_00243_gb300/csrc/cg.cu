@@ -53,6 +53,58 @@ __device__ __forceinline__ void row_chunk(int64_t n, int64_t* r0, int64_t* r1) {
   *r1 = min(n, *r0 + per);
 }
 
+// Dot-product accumulator of the column reductions.  FP64 arithmetic is slow on this
+// part, so the FP32 path accumulates with the compensated "Dot2" scheme of Ogita,
+// Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005):
+// each product is split exactly into p + e (TwoProduct via FMA) and each addition
+// into s + q (Knuth's TwoSum); the error terms are summed separately, which gives the
+// accuracy of a twice-as-precise accumulation.  The warp combine uses the same TwoSum
+// (exact, so every lane of the butterfly ends with the same pair), and only the
+// per-warp result is converted to FP64.  __fmul_rn / __fadd_rn keep the compiler from
+// fusing the steps, which the error-free transformations rely on.
+template <class T>
+struct DotAcc {
+  T s = T(0);
+  __device__ __forceinline__ void add(T x, T y) { s = fma(x, y, s); }
+  __device__ __forceinline__ double warp_total() { return warp_sum(s); }
+};
+template <>
+struct DotAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void two_sum(float a, float b, float& sum, float& err) {
+    sum = __fadd_rn(a, b);
+    const float z = __fadd_rn(sum, -a);
+    err = __fadd_rn(__fadd_rn(a, -__fadd_rn(sum, -z)), __fadd_rn(b, -z));
+  }
+  __device__ __forceinline__ void add(float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float e = fmaf(x, y, -p);              // x y = p + e exactly
+    float q;
+    two_sum(s, p, s, q);
+    c = __fadd_rn(c, __fadd_rn(q, e));
+  }
+  __device__ __forceinline__ double warp_total() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+      float q;
+      two_sum(s, s2, s, q);
+      c = __fadd_rn(__fadd_rn(c, c2), q);
+    }
+    return (double)s + (double)c;
+  }
+};
+
+// Sum of the nb per-block partials of column c, by one warp: lane-strided FP64 sums
+// and a shuffle tree (fixed order, so deterministic); the result is in every lane.
+__device__ __forceinline__ double warp_col_sum(const double* part, int nb, int c) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = lane; b < nb; b += 32) s += part[(size_t)c * nb + b];
+  return warp_sum(s);
+}
+
 // x = 0, r = b, ||b||^2, caps, active set.
 template <class T>
 __global__ void __launch_bounds__(kThreads) cg_init(int64_t n, int t, int max_iter,
@@ -62,23 +114,23 @@ __global__ void __launch_bounds__(kThreads) cg_init(int64_t n, int t, int max_it
   int64_t r0, r1;
   row_chunk(n, &r0, &r1);
   for (int c = warp; c < t; c += kThreads / 32) {
-    double acc = 0.0;
+    DotAcc<T> acc;
     for (int64_t a = r0 + lane; a < r1; a += 32) {
       const T b = g.B[a + c * g.ldb];
       g.X[a + c * n] = T(0);
       g.R[a + c * n] = b;
-      acc += (double)b * (double)b;
+      acc.add(b, b);
     }
-    acc = warp_sum(acc);
-    if (lane == 0) g.part[c * nb + blockIdx.x] = acc;
+    const double sum = acc.warp_total();
+    if (lane == 0) g.part[c * nb + blockIdx.x] = sum;
   }
   if (last_block_arrived(g.counter)) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
-    for (int c = threadIdx.x; c < t; c += blockDim.x) {
-      double s = 0.0;
-      for (int b = 0; b < nb; ++b) s += g.part[c * nb + b];
+    for (int c = warp; c < t; c += kThreads / 32) {
+      const double s = warp_col_sum(g.part, nb, c);
+      if (lane != 0) continue;
       g.bnorm2[c] = s;
       int cap = max_iter;
       int act;
@@ -106,20 +158,23 @@ __global__ void __launch_bounds__(kThreads) cg_init(int64_t n, int t, int max_it
 // and each thread keeps a small register tile of the result.
 
 // (1) S_part[b] = L[rows of part b]^T R[rows of part b] for a 64-pivot slice of S.
-//     Thread (tm, tc) of a 16 x 16 grid owns pivots 4 tm .. 4 tm + 3 and columns
-//     tc, tc + 16, ... (CPT of them).
+//     128 threads; thread (tm, tc) of a 16 x 8 grid owns pivots 4 tm .. 4 tm + 3 and
+//     columns CPT tc .. CPT tc + CPT - 1 (CPT = TC / 8), read from shared memory as
+//     one 16-byte and CPT / 2 8-byte loads per row: 4 CPT FMAs per 1 + CPT / 2 loads.
 constexpr int kLtrRows = 32;
 constexpr int kLtrM = 64;
-constexpr int kLtrParts = 76;     // row parts; x (k / 64) slices ~ 2 CTAs per SM
+constexpr int kLtrParts = 152;    // row parts; x (k / 64) slices ~ 4 CTAs per SM
+constexpr int kLtrThreads = 128;
 template <class T, int TC>
-__global__ void __launch_bounds__(kThreads) ltr_partial(int64_t n, int t, const T* __restrict__ L,
-                                                       int64_t ldl, int k, Dev<T> g) {
+__global__ void __launch_bounds__(kLtrThreads) ltr_partial(int64_t n, int t,
+                                                          const T* __restrict__ L, int64_t ldl,
+                                                          int k, Dev<T> g) {
   if (*g.n_active == 0) return;
-  constexpr int CPT = TC / 16;
-  // padded so that the coalesced staging stores and the compute reads both stay
-  // (nearly) free of bank conflicts
-  __shared__ T sL[kLtrM][kLtrRows + 1];
-  __shared__ T sR[kLtrRows][TC + 1];
+  constexpr int CPT = TC / 8;
+  constexpr int LP = kLtrM + 16 / (int)sizeof(T);   // row pitch: 16-byte aligned rows
+  constexpr int RP = TC + 2;
+  __shared__ __align__(16) T sL[kLtrRows][LP];
+  __shared__ __align__(16) T sR[kLtrRows][RP];
   const int tm = threadIdx.x & 15, tcol = threadIdx.x >> 4;
   const int m0 = blockIdx.x * kLtrM;
   const int64_t per = (n + gridDim.y - 1) / gridDim.y;
@@ -132,42 +187,44 @@ __global__ void __launch_bounds__(kThreads) ltr_partial(int64_t n, int t, const 
   for (int64_t rb = r0; rb < r1; rb += kLtrRows) {
     const int rn = (int)min((int64_t)kLtrRows, r1 - rb);
     __syncthreads();
-    for (int e = threadIdx.x; e < kLtrRows * kLtrM; e += kThreads) {
+    for (int e = threadIdx.x; e < kLtrRows * kLtrM; e += kLtrThreads) {
       const int rr = e % kLtrRows, mm = e / kLtrRows;     // rows fastest: coalesced
-      sL[mm][rr] = (rr < rn && m0 + mm < k) ? L[rb + rr + (int64_t)(m0 + mm) * ldl] : T(0);
+      sL[rr][mm] = (rr < rn && m0 + mm < k) ? L[rb + rr + (int64_t)(m0 + mm) * ldl] : T(0);
     }
-    for (int e = threadIdx.x; e < kLtrRows * TC; e += kThreads) {
+    for (int e = threadIdx.x; e < kLtrRows * TC; e += kLtrThreads) {
       const int rr = e % kLtrRows, c = e / kLtrRows;
       sR[rr][c] = (rr < rn && c < t) ? g.R[rb + rr + (int64_t)c * n] : T(0);
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int rr = 0; rr < kLtrRows; ++rr) {
-      T lv[4];
+      T lv[4], rv[CPT];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) lv[a] = sL[tm * 4 + a][rr];
+      for (int a = 0; a < 4; ++a) lv[a] = sL[rr][tm * 4 + a];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        const T rv = sR[rr][tcol + 16 * c];
+      for (int c = 0; c < CPT; ++c) rv[c] = sR[rr][tcol * CPT + c];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][c] = fma(lv[a], rv, acc[a][c]);
-      }
+      for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][c] = fma(lv[a], rv[c], acc[a][c]);
     }
   }
-  double* out = g.S + (size_t)blockIdx.y * k * t;     // per-part partials (k x t)
+  double* out = g.S + (size_t)blockIdx.y * k * t;     // per-part partials (t x k)
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int m = m0 + tm * 4 + a;
     if (m >= k) continue;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-      const int col = tcol + 16 * c;
-      if (col < t) out[(size_t)m * t + col] = (double)acc[a][c];
+      const int col = tcol * CPT + c;
+      if (col < t) out[(size_t)col * k + m] = (double)acc[a][c];
     }
   }
 }
 
 // (2) S = sum of the part partials (FP64), Sp = C^-1 S (FP64), for active columns.
+//     C^-1 is exactly symmetric (formed as Gc^-T Gc^-1 with one summation order), so
+//     Sp_i = sum_m C^-1[m][i] S_m reads rows of C^-1 coalesced across threads i.
 template <class T>
 __global__ void reduce_cinv(int k, int t, int ldsp, int nparts, const double* __restrict__ Cinv,
                             const double* __restrict__ part, Dev<T> g) {
@@ -176,27 +233,31 @@ __global__ void reduce_cinv(int k, int t, int ldsp, int nparts, const double* __
   const int c = blockIdx.y;
   if (!g.active[c]) return;
   for (int m = threadIdx.x; m < k; m += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[((size_t)b * k + m) * t + c];
-    sS[m] = s;
+    double s0 = 0.0, s1 = 0.0;       // two chains over the parts (fixed order)
+    int b = 0;
+    for (; b + 1 < nparts; b += 2) {
+      s0 += part[((size_t)b * t + c) * k + m];
+      s1 += part[((size_t)(b + 1) * t + c) * k + m];
+    }
+    if (b < nparts) s0 += part[((size_t)b * t + c) * k + m];
+    sS[m] = s0 + s1;
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= k) return;
-  const double* crow = Cinv + (int64_t)i * k;
   double a0 = 0.0, a1 = 0.0;
   int m = 0;
   for (; m + 1 < k; m += 2) {
-    a0 += crow[m] * sS[m];
-    a1 += crow[m + 1] * sS[m + 1];
+    a0 += Cinv[(int64_t)m * k + i] * sS[m];
+    a1 += Cinv[(int64_t)(m + 1) * k + i] * sS[m + 1];
   }
-  if (m < k) a0 += crow[m] * sS[m];
+  if (m < k) a0 += Cinv[(int64_t)m * k + i] * sS[m];
   g.Sp[(int64_t)i * ldsp + c] = (T)(a0 + a1);
 }
 
 // (3) z = sigma^-2 (r - L Sp) and the partial sums of r^T z for active columns, one
 //     128-row tile per block.  Thread (tr, tc) of a 32 x 8 grid owns rows
-//     4 tr .. 4 tr + 3 and columns tc, tc + 8, ... (CPT of them).
+//     4 tr .. 4 tr + 3 and columns CPT tc .. CPT tc + CPT - 1.
 constexpr int kPrRows = 128;
 constexpr int kPrM = 32;
 template <class T, int TC>
@@ -234,22 +295,23 @@ __global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, int c0
     __syncthreads();
 #pragma unroll 8
     for (int mm = 0; mm < kPrM; ++mm) {
-      T lv[4];
+      T lv[4], sv[CPT];
 #pragma unroll
       for (int a = 0; a < 4; ++a) lv[a] = sL[mm][tr * 4 + a];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        const T sv = sSp[mm][tcol + 8 * c];
+      for (int c = 0; c < CPT; ++c) sv[c] = sSp[mm][tcol * CPT + c];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][c] = fma(lv[a], sv, acc[a][c]);
-      }
+      for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][c] = fma(lv[a], sv[c], acc[a][c]);
     }
   }
-  // z, and r^T z summed over this block's rows per column
+  // z, and r^T z summed over this block's rows per column (compensated FP32 within
+  // the block, FP64 across blocks)
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
-    const int col = tcol + 8 * c;
-    double rz = 0.0;
+    const int col = tcol * CPT + c;
+    DotAcc<T> rz;
     if (col < tc && g.active[c0 + col]) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -259,18 +321,18 @@ __global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, int c0
           const T r = g.R[off];
           const T z = (r - acc[a][c]) * inv_s2;
           g.Z[off] = z;
-          rz += (double)r * (double)z;
+          rz.add(r, z);
         }
       }
     }
-    rz = warp_sum(rz);                  // the warp's 32 threads share column col
-    if (tr == 0) swarp[warp][c] = rz;   // warp index == tcol
+    const double rzw = rz.warp_total();           // the warp's 32 threads share column col
+    if (tr == 0) swarp[warp][c] = rzw;            // warp index == tcol
   }
   __syncthreads();
   const int nb = gridDim.x;
   for (int col = threadIdx.x; col < tc; col += blockDim.x) {
-    // column col is owned by warp (col % 8), slot (col / 8)
-    g.part[(size_t)(c0 + col) * nb + blockIdx.x] = swarp[col % 8][col / 8];
+    // column col is owned by warp (col / CPT), slot (col % CPT)
+    g.part[(size_t)(c0 + col) * nb + blockIdx.x] = swarp[col / CPT][col % CPT];
   }
 }
 
@@ -278,10 +340,11 @@ __global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, int c0
 template <class T>
 __global__ void rho_combine(int t, int nb, int mode, int j, int max_iter, Dev<T> g) {
   if (*g.n_active == 0) return;
-  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < t; c += blockDim.x >> 5) {
     if (!g.active[c]) continue;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += g.part[(size_t)c * nb + b];
+    const double s = warp_col_sum(g.part, nb, c);
+    if (lane != 0) continue;
     if (mode == 0) {
       g.rho[c] = s;
       g.rho0[c] = s;
@@ -324,17 +387,16 @@ __global__ void __launch_bounds__(kThreads) cg_alpha(int64_t n, int t, int j, in
   row_chunk(n, &r0, &r1);
   for (int c = warp; c < t; c += kThreads / 32) {
     if (!g.active[c]) continue;
-    double acc = 0.0;
-    for (int64_t a = r0 + lane; a < r1; a += 32)
-      acc += (double)g.P[a + c * n] * (double)g.Q[a + c * n];
-    acc = warp_sum(acc);
-    if (lane == 0) g.part[c * nb + blockIdx.x] = acc;
+    DotAcc<T> acc;
+    for (int64_t a = r0 + lane; a < r1; a += 32) acc.add(g.P[a + c * n], g.Q[a + c * n]);
+    const double sum = acc.warp_total();
+    if (lane == 0) g.part[c * nb + blockIdx.x] = sum;
   }
   if (last_block_arrived(g.counter)) {
-    for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    for (int c = warp; c < t; c += kThreads / 32) {
       if (!g.active[c]) continue;
-      double pq = 0.0;
-      for (int b = 0; b < nb; ++b) pq += g.part[c * nb + b];
+      const double pq = warp_col_sum(g.part, nb, c);
+      if (lane != 0) continue;
       double al = g.rho[c] / pq;
       if (!(pq > 0.0) || !isfinite(al)) {
         *g.status = GP_ERR_NUMERIC;
@@ -349,18 +411,19 @@ __device__ void decide(int t, int j, const double* rnorm2_part, int nb, double t
                        int use_caps, int max_iter, int* active, const int* caps, int* iters,
                        const double* bnorm2, int* n_active) {
   __shared__ int cnt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
-  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+  for (int c = warp; c < t; c += blockDim.x >> 5) {
     if (!active[c]) continue;
     bool stop;
     if (use_caps) {
       stop = (j + 1) >= caps[c];
     } else {
-      double s = 0.0;
-      for (int b = 0; b < nb; ++b) s += rnorm2_part[c * nb + b];
+      const double s = warp_col_sum(rnorm2_part, nb, c);
       stop = (s <= tol2 * bnorm2[c]) || (j + 1 >= max_iter);
     }
+    if (lane != 0) continue;
     if (stop) {
       active[c] = 0;
       iters[c] = j + 1;
@@ -385,16 +448,16 @@ __global__ void __launch_bounds__(kThreads) cg_update(int64_t n, int t, int j, i
   for (int c = warp; c < t; c += kThreads / 32) {
     if (!g.active[c]) continue;
     const T al = (T)g.alpha[(int64_t)c * max_iter + j];
-    double acc = 0.0;
+    DotAcc<T> acc;
     for (int64_t a = r0 + lane; a < r1; a += 32) {
       const int64_t off = a + c * n;
       g.X[off] = fma(al, g.P[off], g.X[off]);
       const T r = fma(-al, g.Q[off], g.R[off]);
       g.R[off] = r;
-      acc += (double)r * (double)r;
+      acc.add(r, r);
     }
-    acc = warp_sum(acc);
-    if (lane == 0 && !recompute) g.part[c * nb + blockIdx.x] = acc;
+    const double sum = acc.warp_total();
+    if (lane == 0 && !recompute) g.part[c * nb + blockIdx.x] = sum;
   }
   if (recompute) return;
   if (last_block_arrived(g.counter))
@@ -412,15 +475,15 @@ __global__ void __launch_bounds__(kThreads) cg_resid(int64_t n, int t, int j, in
   row_chunk(n, &r0, &r1);
   for (int c = warp; c < t; c += kThreads / 32) {
     if (!g.active[c]) continue;
-    double acc = 0.0;
+    DotAcc<T> acc;
     for (int64_t a = r0 + lane; a < r1; a += 32) {
       const int64_t off = a + c * n;
       const T r = g.B[a + c * g.ldb] - g.Q[off];
       g.R[off] = r;
-      acc += (double)r * (double)r;
+      acc.add(r, r);
     }
-    acc = warp_sum(acc);
-    if (lane == 0) g.part[c * nb + blockIdx.x] = acc;
+    const double sum = acc.warp_total();
+    if (lane == 0) g.part[c * nb + blockIdx.x] = sum;
   }
   if (last_block_arrived(g.counter))
     decide(t, j, g.part, nb, tol2, use_caps, max_iter, g.active, g.caps, g.iters, g.bnorm2,
@@ -502,13 +565,13 @@ gp_status precond_apply(int64_t n, int t, const T* L, int64_t ldl, int k, const 
       gc.S = cb.atb_part;
       dim3 grid((unsigned)cdiv(k, kLtrM), (unsigned)kLtrParts);
       GP_TC_DISPATCH(pick_tc16(tc),
-                     (ltr_partial<T, TC><<<grid, kThreads, 0, st>>>(n, tc, L, ldl, k, gc)));
+                     (ltr_partial<T, TC><<<grid, kLtrThreads, 0, st>>>(n, tc, L, ldl, k, gc)));
       GP_LAUNCH_CHECK();
       Dev<T> gs = g;                 // Sp columns c0.. (leading dimension t)
       gs.active = g.active + c0;
       gs.Sp = g.Sp + c0;
-      dim3 g2((unsigned)cdiv(k, 128), (unsigned)tc);
-      reduce_cinv<T><<<g2, 128, sizeof(double) * k, st>>>(k, tc, t, kLtrParts, Cinv,
+      dim3 g2((unsigned)cdiv(k, 256), (unsigned)tc);
+      reduce_cinv<T><<<g2, 256, sizeof(double) * k, st>>>(k, tc, t, kLtrParts, Cinv,
                                                          cb.atb_part, gs);
       GP_LAUNCH_CHECK();
     }

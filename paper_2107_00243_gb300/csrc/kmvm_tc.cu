@@ -656,32 +656,47 @@ __global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __r
 
 // Power-of-two column scales of V: scale_c = 2^e_c with max_j |V_jc| scale_c in
 // [2^13, 2^14) (1 for an all-zero or non-finite column).  vscale[c] = scale_c,
-// vscale[kMaxT64 + c] = 1 / scale_c.  One block per column.
+// vscale[kMaxT64 + c] = 1 / scale_c.  Grid (kScaleParts, t): block (b, c) takes the
+// maximum over one row range of column c into vscale[2 kMaxT64 + c kScaleParts + b];
+// the last block of column c to finish (counter cnt[c], reset by that block) forms
+// the scale.
 constexpr int kMaxT64 = 64;
+constexpr int kScaleParts = 16;
 __global__ void colscale_kernel(int n, const float* __restrict__ V, int64_t ldv,
-                                float* __restrict__ vscale, const int* gate) {
+                                float* __restrict__ vscale, unsigned* __restrict__ cnt,
+                                const int* gate) {
   if (gate && *gate == 0) return;
-  const int c = blockIdx.x;
+  const int c = blockIdx.y, b = blockIdx.x;
+  const int per = (n + kScaleParts - 1) / kScaleParts;
+  const int r0 = b * per, r1 = min(n, r0 + per);
   float m = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(V[i + (int64_t)c * ldv]));
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) m = fmaxf(m, fabsf(V[i + (int64_t)c * ldv]));
   __shared__ float red[32];
+  __shared__ bool last;
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) {
-      int e = 0;
-      if (m > 0.f && m <= 3.0e38f) {
-        int ex;
-        frexpf(m, &ex);                       // m = f 2^ex, f in [0.5, 1)
-        e = max(-120, min(120, 14 - ex));     // m 2^e in [2^13, 2^14)
-      }
-      vscale[c] = ldexpf(1.0f, e);
-      vscale[kMaxT64 + c] = ldexpf(1.0f, -e);
-    }
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    vscale[2 * kMaxT64 + c * kScaleParts + b] = m;
+    __threadfence();
+    last = atomicAdd(&cnt[c], 1u) == kScaleParts - 1;
   }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  const volatile float* parts = vscale + 2 * kMaxT64 + c * kScaleParts;
+  float mx = 0.f;
+  for (int q = 0; q < kScaleParts; ++q) mx = fmaxf(mx, parts[q]);
+  int e = 0;
+  if (mx > 0.f && mx <= 3.0e38f) {
+    int ex;
+    frexpf(mx, &ex);                      // mx = f 2^ex, f in [0.5, 1)
+    e = max(-120, min(120, 14 - ex));     // mx 2^e in [2^13, 2^14)
+  }
+  vscale[c] = ldexpf(1.0f, e);
+  vscale[kMaxT64 + c] = ldexpf(1.0f, -e);
+  cnt[c] = 0;
 }
 
 // V (n x t FP32, column-major) -> tiles of 2 tp x BN FP16: rows [0, tp) the hi parts
@@ -807,7 +822,8 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
   __half* vp = static_cast<__half*>(tb.vpack);
   int* err = tb.err;
   const int64_t vtotal = (int64_t)nt * BN * tp;
-  colscale_kernel<<<t, 256, 0, st>>>(n, V, ldv, tb.vscale, gate);
+  colscale_kernel<<<dim3(kScaleParts, t), 256, 0, st>>>(
+      n, V, ldv, tb.vscale, reinterpret_cast<unsigned*>(tb.err + kTcErrCounters), gate);
   GP_LAUNCH_CHECK();
   pack_v_kernel<<<(unsigned)cdiv(vtotal, 256), 256, 0, st>>>(n, nt, t, tp, V, ldv, tb.vscale, vp,
                                                               gate);

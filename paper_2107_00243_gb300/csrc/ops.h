@@ -41,10 +41,13 @@ struct TcBufs {
   void* xpack;       // packed hi/lo operand tiles of the scaled inputs
   float* norms;      // n
   void* vpack;       // packed right-hand-side tiles
-  float* vscale;     // 128: power-of-two column scales of V and their inverses
+  float* vscale;     // kTcVscaleElems: column scales of V, their inverses, partial maxima
   float* part;       // split partial sums
-  int* err;          // 2 ints: device-side status and the wait that gave up
+  int* err;          // kTcErrInts: device-side status, the wait that gave up, counters
 };
+constexpr int kTcErrCounters = 4;               // err[4 ..]: per-column block counters
+constexpr int kTcErrInts = kTcErrCounters + 64;
+constexpr int kTcVscaleElems = 2 * 64 + 64 * 16;
 size_t tc_xpack_bytes(int64_t n, int d, int prec);
 size_t tc_vpack_bytes(int64_t n, int t, int prec);
 size_t tc_part_elems(int64_t n, int t);

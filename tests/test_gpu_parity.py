@@ -13,8 +13,9 @@ diagonal has a near tie (both picks are then valid greedy choices).
 Why the estimator bounds are what they are.  CG iterates stopped at a loose
 tolerance are sensitive to rounding once orthogonality is lost: the FP64 oracle
 itself moves when only the summation order of its kernel products changes
-(measured: 2.4e-9 on the MLL and 2.2e-7 on gradient entries of the small RBF
-workload).  Hence the FP64 bounds of 1e-8 (values) and 1e-6 (gradients).  In
+(measured on the small RBF workload over row blockings of 37, 64, 128 and 333: up
+to 4.9e-9 on the MLL, 7.1e-9 on the quadratic term y^T u, and 2.2e-7 on gradient
+entries).  Hence the FP64 bounds of 2e-8 (values) and 1e-6 (gradients).  In
 FP32 the benchmark spec's bound of 1e-4 holds on every result when CG runs to a tight
 tolerance (test_estimator_matern52_ard_fp32_tight); at the Matern-5/2 workload's
 own tolerance of 1e-3 the oracle's gradients move by up to 5.8e-4 under
@@ -31,7 +32,7 @@ from paper_2107_00243_gb300 import gp, workloads
 pytestmark = pytest.mark.gpu
 
 KTOL = {gp.FP64: 1e-11, gp.FP32: 2e-5}
-ETOL = {gp.FP64: (1e-8, 1e-6), gp.FP32: (1e-4, 1e-4)}   # (values, gradient entries)
+ETOL = {gp.FP64: (2e-8, 1e-6), gp.FP32: (1e-4, 1e-4)}   # (values, gradient entries)
 
 
 @pytest.fixture(scope="module", autouse=True)
