@@ -89,8 +89,25 @@ typedef struct {
   uint64_t seed;           /* probe seed (counter-based SplitMix64 hash)          */
   double pivchol_tol;      /* stop pivoted Cholesky when tr(K - LL^T) <= tol tr K */
   int32_t check_every;     /* host polls CG convergence every this many steps (0 = 4) */
-  int32_t reserved;
+  int32_t flags;           /* GP_OPT_* bits (0: defaults)                          */
 } gp_opts;
+
+/* gp_opts.flags.  In GP_BF16 precision the kernel product rounds k(r)/s to FP16
+ * (11 significant bits).  For smooth kernels with small noise (lambda_max(K) /
+ * sigma^2 large) that rounding can make K + sigma^2 I indefinite and CG break down
+ * (p^T K_hat p <= 0).  The product then has a split mode that carries k(r)/s as FP16
+ * hi + lo (22 bits) at about twice the GEMM2 work.
+ *   default           fast mode; an eager call (stream not being captured) whose
+ *                     CG breaks down reruns CG in split mode.
+ *   GP_OPT_SPLIT_P    split mode from the start.
+ *   GP_OPT_AUTO_SPLIT choose on the device before CG, from the Gershgorin bound
+ *                     lambda_max(K_hat) <= max_i sum_j K_hat_ij (one extra product
+ *                     with a vector of ones): split when 2^-11 * bound > 8 sigma^2.
+ *                     For graph capture and batched calls, where the host cannot
+ *                     rerun CG.  Conservative: some problems it splits would have
+ *                     run in fast mode.                                           */
+#define GP_OPT_SPLIT_P 1
+#define GP_OPT_AUTO_SPLIT 2
 
 /* Which entry point a workspace query is for. */
 typedef enum {
@@ -183,12 +200,41 @@ gp_status gp_mbcg(const gp_problem* prob, const void* L, int64_t ldl, int32_t k,
  * leading dim k + n: rows 0..k-1 eps1, rows k.. eps2; or NULL = SplitMix64 from
  * opts->seed), piv_override (k int32 or NULL), iters_override (t int32 or NULL)
  * exist for parity testing.  out: GP_OUT_LEN(p, n_probes) doubles; iout:
- * GP_IOUT_LEN(k, t) int32.  Synchronises with `stream`.                          */
+ * GP_IOUT_LEN(k, t) int32.  Synchronises with `stream`, except while `stream` is
+ * being captured into a CUDA graph: then nothing is read back, mBCG's iteration
+ * loop is recorded as a conditional WHILE node (the stopping rule is evaluated on
+ * the device), the call returns GP_OK, and the status of the evaluation is
+ * iout[GP_IOUT_STATUS] once the graph has run.                                   */
 gp_status gp_mll_and_grad(const gp_problem* prob, const void* y, int32_t k,
                           int32_t n_probes, const int8_t* eps_override,
                           const int32_t* piv_override, const int32_t* iters_override,
                           double* out, int32_t* iout, const gp_opts* opts, void* ws,
                           size_t ws_bytes, gp_stream_t stream);
+
+/* Batched estimator: n_problems independent problems (each its own n, d, X,
+ * hyperparameters and precision; shared k, n_probes and opts; problem i draws its
+ * probes from seed opts->seed + i).  The per-probe loops of Alg. 1 and Alg. 2 are
+ * independent (the footnote to Sec. 4.4 batches them into one CG call); independent
+ * problems are one more level of the same parallelism.  probs: host array; ys, outs,
+ * iouts: host arrays of device pointers (per problem: n reals, GP_OUT_LEN(p_i,
+ * n_probes) doubles, GP_IOUT_LEN(k, n_probes + 1) int32).  ws: device, at least
+ * gp_workspace_size_batched(...) bytes, 256-byte aligned; problem i uses its own
+ * slice, so results equal those of gp_mll_and_grad on that slice.
+ * Execution: the problems run concurrently on up to 8 worker streams (largest
+ * first, to the least-loaded worker), recorded as one CUDA graph with device-side
+ * CG loops; the instantiated graph is cached per argument set (pointers, sizes,
+ * options; up to 4 per host thread), so repeating a call with new values in the
+ * same buffers is a single graph launch.  If `stream` is being captured, the batch
+ * is recorded into the caller's graph instead.  Asynchronous: returns after the
+ * launch; per-problem statuses are iouts[i][GP_IOUT_STATUS] once `stream` reaches
+ * that point.  Host-side validation errors return before anything is launched.   */
+size_t gp_workspace_size_batched(int32_t n_problems, const gp_problem* probs, int32_t k,
+                                 int32_t n_probes, int32_t max_iter);
+gp_status gp_mll_and_grad_batched(int32_t n_problems, const gp_problem* probs,
+                                  const void* const* ys, int32_t k, int32_t n_probes,
+                                  double* const* outs, int32_t* const* iouts,
+                                  const gp_opts* opts, void* ws, size_t ws_bytes,
+                                  gp_stream_t stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* gp_status_string(int32_t status);

@@ -2,6 +2,8 @@
 // the order of the estimator's steps (Alg. 1 and Alg. 2 fused into one CG call).
 #include <cstdarg>
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "ops.h"
 
@@ -122,6 +124,7 @@ void plan_cg(Arena& A, const Prob& pb, int k, int t, int max_iter, CgBufs<T>& c)
   c.n_active = A.take<int>(1);
   c.status = A.take<int>(1);
   c.counter = A.take<unsigned>(4);
+  c.ctl = A.take<int>(4);
 }
 
 struct CorePlan {
@@ -209,7 +212,7 @@ __global__ void fill_weights(int t, double* w) {
 }
 
 __global__ void assemble(int64_t n, int P, int nl, int k, const int* rank, const int* iters,
-                         const int* piv, const int* dev_status, const int* rank_stat,
+                         const int* piv, const int* dev_status, const int* tc_err,
                          double* out, int* iout) {
   if (threadIdx.x != 0) return;
   const double LOG2PI = 1.8378770664093453;
@@ -224,11 +227,12 @@ __global__ void assemble(int64_t n, int P, int nl, int k, const int* rank, const
                               0.5 * out[GP_OUT_TRP(P) + q];
   for (int h = 5; h < GP_OUT_HEAD; ++h) out[h] = 0.0;
   const int t = nl + 1;
-  iout[GP_IOUT_STATUS] = *dev_status;
+  // a tensor-core product that gave up waiting (its outputs are NaN) outranks the
+  // CG status
+  iout[GP_IOUT_STATUS] = (tc_err && tc_err[0] < 0) ? tc_err[0] : *dev_status;
   iout[GP_IOUT_RANK] = *rank;
   for (int c = 0; c < t; ++c) iout[GP_IOUT_ITERS + c] = iters[c];
   for (int m = 0; m < k; ++m) iout[GP_IOUT_PIV(t) + m] = piv[m];
-  (void)rank_stat;
 }
 
 template <class T>
@@ -237,24 +241,84 @@ __global__ void copy_col(int64_t n, const T* src, T* dst) {
   if (a < n) dst[a] = src[a];
 }
 
-// A non-blocking side stream and two events per host thread and device.
+// Non-blocking side streams with two events each, per host thread and device: index
+// 0 serves single calls, 1 .. kBatchStreams the worker streams of a batched call.
+constexpr int kBatchStreams = 8;
 struct SideStream {
   cudaStream_t stream = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   int device = -1;
   bool ok = false;
 };
-SideStream& side_stream() {
-  static thread_local SideStream ss;
+SideStream& side_stream(int i = 0) {
+  static thread_local SideStream ss[kBatchStreams + 1];
+  SideStream& s = ss[i];
   int dev = 0;
   cudaGetDevice(&dev);
-  if (!ss.ok || ss.device != dev) {
-    ss.ok = cudaStreamCreateWithFlags(&ss.stream, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) == cudaSuccess;
-    ss.device = dev;
+  if (!s.ok || s.device != dev) {
+    s.ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming) == cudaSuccess;
+    s.device = dev;
   }
-  return ss;
+  return s;
+}
+
+// ---- split mode of the tensor-core product (GP_OPT_*) ----------------------------------
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+
+template <class T>
+__global__ void fill_ones(int64_t n, T* x) {
+  int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a < n) x[a] = T(1);
+}
+
+// flag = 1 when 2^-11 max_i (K_hat 1)_i > 8 sigma^2 (Gershgorin bound on lambda_max).
+template <class T>
+__global__ void split_decide(int64_t n, const T* __restrict__ rowsum,
+                             const double* __restrict__ theta, int D, int* flag) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (int64_t a = threadIdx.x; a < n; a += blockDim.x) m = fmax(m, (double)rowsum[a]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    const double s2 = theta[D + 1];
+    *flag = (m * 0.00048828125 > 8.0 * s2) ? 1 : 0;
+  }
+}
+
+// Sets the split flag (err[2]) of the TC product before CG: forced, or from the
+// Gershgorin bound (one product of K_hat with a vector of ones, into scratch
+// columns that CG overwrites afterwards).
+template <class T>
+gp_status tc_split_setup(const Prob& pb, MvmOp& op, const TcBufs& tb, T* ones, T* rowsum,
+                         const gp_opts& o, cudaStream_t st) {
+  if (o.flags & GP_OPT_SPLIT_P) {
+    set_int_kernel<<<1, 1, 0, st>>>(tb.err + 2, 1);
+    GP_LAUNCH_CHECK();
+  } else if (o.flags & GP_OPT_AUTO_SPLIT) {
+    fill_ones<T><<<(unsigned)cdiv(pb.n, 256), 256, 0, st>>>(pb.n, ones);
+    GP_LAUNCH_CHECK();
+    GP_TRY(op.apply(ones, pb.n, 1, rowsum, pb.n, nullptr, st));
+    split_decide<T><<<1, 1024, 0, st>>>(pb.n, rowsum, pb.theta, pb.D, tb.err + 2);
+    GP_LAUNCH_CHECK();
+  }
+  return GP_OK;
+}
+
+// After an eager CG call that broke down in fast mode: true (and split mode set)
+// when CG should run again.
+inline bool tc_retry_split(const TcBufs& tb, int host_status, cudaStream_t st) {
+  if (host_status != GP_ERR_NUMERIC) return false;
+  int flag = 1;
+  if (cudaMemcpyAsync(&flag, tb.err + 2, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess || flag != 0)
+    return false;
+  set_int_kernel<<<1, 1, 0, st>>>(tb.err + 2, 1);
+  return cudaGetLastError() == cudaSuccess;
 }
 
 // ---- gp_mll_and_grad plan -----------------------------------------------------------
@@ -297,7 +361,8 @@ void plan_mll(Arena& A, const Prob& pb, int k, int nl, int max_iter, MllPlan<T>&
 template <class T>
 gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
                    const int* piv_override, const int* iters_override, double* out, int* iout,
-                   const gp_opts& o, void* ws, size_t ws_bytes, cudaStream_t st) {
+                   const gp_opts& o, void* ws, size_t ws_bytes, cudaStream_t st,
+                   int side_index = 0) {
   const int t = nl + 1;
   MllPlan<T> P;
   {
@@ -338,8 +403,14 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
     TcMvm op;
     op.pb = pb;
     op.tb = P.mvm.tc;
+    GP_TRY(tc_split_setup<T>(pb, op, P.mvm.tc, P.cg.Q, P.cg.R, o, st));
     GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o, P.cg,
                        P.PinvB, pb.n, &host_status, st));
+    if (tc_retry_split(P.mvm.tc, host_status, st)) {
+      GP_CUDA_TRY(cudaMemsetAsync(P.cg.status, 0, sizeof(int), st));
+      GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o,
+                         P.cg, P.PinvB, pb.n, &host_status, st));
+    }
   } else {
     SimtMvm<T> op;
     op.pb = pb;
@@ -350,7 +421,7 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   }
   // S8: Lanczos quadrature per probe.  It needs only the CG coefficients, uses one
   // block per probe, and runs on a side stream next to S9 and S10.
-  SideStream& side = side_stream();
+  SideStream& side = side_stream(side_index);
   if (!side.ok) {
     set_error("could not create the side stream");
     return GP_ERR_CUDA;
@@ -376,8 +447,14 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   // S11: assembly
   GP_CUDA_TRY(cudaStreamWaitEvent(st, side.join, 0));
   assemble<<<1, 32, 0, st>>>(pb.n, pb.p, nl, k, P.rank, P.cg.iters, P.pivots, P.cg.status,
-                             nullptr, out, iout);
+                             P.mvm.use_tc ? P.mvm.tc.err : nullptr, out, iout);
   GP_LAUNCH_CHECK();
+
+  // under stream capture nothing is read back: the statuses are in iout once the
+  // graph has run
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GP_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap == cudaStreamCaptureStatusActive) return GP_OK;
 
   int hstat = 0, hrank = 0, herr[2] = {0, 0};
   GP_CUDA_TRY(cudaMemcpyAsync(&hstat, P.cg.status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -613,8 +690,14 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
     TcMvm op;
     op.pb = pb;
     op.tb = mp.tc;
+    GP_TRY(tc_split_setup<T>(pb, op, mp.tc, cb.Q, cb.R, o, st));
     GP_TRY(cg_solve<T>(pb, op, L, ldl, k, cp.Cinv, B, ldb, t, iters_override, o, cb, PinvB, ldx,
                        &host_status, st));
+    if (tc_retry_split(mp.tc, host_status, st)) {
+      GP_CUDA_TRY(cudaMemsetAsync(cb.status, 0, sizeof(int), st));
+      GP_TRY(cg_solve<T>(pb, op, L, ldl, k, cp.Cinv, B, ldb, t, iters_override, o, cb, PinvB,
+                         ldx, &host_status, st));
+    }
   } else {
     SimtMvm<T> op;
     op.pb = pb;
@@ -630,6 +713,9 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
   GP_CUDA_TRY(cudaMemcpyAsync(rho0, cb.rho0, sizeof(double) * t, cudaMemcpyDeviceToDevice, st));
   GP_CUDA_TRY(cudaMemcpyAsync(iters, cb.iters, sizeof(int) * t, cudaMemcpyDeviceToDevice, st));
   GP_CUDA_TRY(cudaMemcpyAsync(status, cb.status, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GP_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap == cudaStreamCaptureStatusActive) return GP_OK;   // status read after the graph runs
   int hs = 0, herr[2] = {0, 0};
   GP_CUDA_TRY(cudaMemcpyAsync(&hs, cb.status, sizeof(int), cudaMemcpyDeviceToHost, st));
   if (mp.use_tc)
@@ -695,6 +781,221 @@ extern "C" gp_status gp_mll_and_grad(const gp_problem* prob, const void* y, int3
                             iters_override, out, iout, *opts, ws, ws_bytes, st);
   return mll_impl<float>(pb, (const float*)y, k, n_probes, eps_override, piv_override,
                          iters_override, out, iout, *opts, ws, ws_bytes, st);
+}
+
+// ---- batched evaluation --------------------------------------------------------------
+// Independent problems run concurrently on a pool of worker streams (each problem's
+// own steps stay in order on one stream; its Lanczos quadrature forks to a side
+// stream of that worker).  The whole batch is recorded as one CUDA graph: mBCG's
+// iteration loops become conditional WHILE nodes (no host round trips), and the
+// instantiated graph is cached per argument set, so a repeated call (for example an
+// optimiser step with new hyperparameter values in the same device buffers) is a
+// single graph launch.  When the caller's stream is itself being captured, the batch
+// is recorded into the caller's graph instead.
+namespace gp {
+namespace {
+
+struct StreamPool {
+  cudaStream_t s[kBatchStreams] = {};
+  cudaStream_t capture = nullptr;
+  cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
+  int device = -1;
+  bool ok = false;
+};
+StreamPool& stream_pool() {
+  static thread_local StreamPool p;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!p.ok || p.device != dev) {
+    bool ok = cudaStreamCreateWithFlags(&p.capture, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int w = 0; w < kBatchStreams && ok; ++w)
+      ok = cudaStreamCreateWithFlags(&p.s[w], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&p.join[w], cudaEventDisableTiming) == cudaSuccess;
+    p.ok = ok;
+    p.device = dev;
+  }
+  return p;
+}
+
+constexpr size_t kBatchAlign = 256;
+size_t batch_layout(int np, const Prob* pbs, int k, int t, int max_iter, size_t* offs,
+                    size_t* sizes) {
+  size_t off = 0;
+  for (int i = 0; i < np; ++i) {
+    const size_t sz = gp_workspace_size(GP_FN_MLL_AND_GRAD, pbs[i].n, pbs[i].d, k, t, pbs[i].prec,
+                                        max_iter);
+    if (offs) offs[i] = off;
+    if (sizes) sizes[i] = sz;
+    off += (sz + kBatchAlign - 1) / kBatchAlign * kBatchAlign;
+  }
+  return off;
+}
+
+// Issue every problem of the batch on the worker streams, forked from and joined back
+// into `origin` (which is being captured).  Largest problems first, each to the
+// worker with the least work so far (work ~ n^2).
+gp_status issue_batch(int np, const Prob* pbs, const void* const* ys, int k, int nl,
+                      double* const* outs, int* const* iouts, const gp_opts& o, char* ws,
+                      const size_t* offs, const size_t* sizes, cudaStream_t origin) {
+  StreamPool& P = stream_pool();
+  if (!P.ok) {
+    set_error("could not create the batch streams");
+    return GP_ERR_CUDA;
+  }
+  const int nw = std::min(np, kBatchStreams);
+  std::vector<int> order(np);
+  for (int i = 0; i < np; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return pbs[a].n > pbs[b].n; });
+  std::vector<double> load(nw, 0.0);
+  GP_CUDA_TRY(cudaEventRecord(P.fork, origin));
+  for (int w = 0; w < nw; ++w) GP_CUDA_TRY(cudaStreamWaitEvent(P.s[w], P.fork, 0));
+  for (int i : order) {
+    const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[w] += (double)pbs[i].n * (double)pbs[i].n;
+    gp_opts oi = o;
+    oi.seed = o.seed + (uint64_t)i;   // problem i draws its probes from seed + i
+    gp_status r;
+    if (pbs[i].prec == GP_FP64)
+      r = mll_impl<double>(pbs[i], (const double*)ys[i], k, nl, nullptr, nullptr, nullptr,
+                           outs[i], iouts[i], oi, ws + offs[i], sizes[i], P.s[w], 1 + w);
+    else
+      r = mll_impl<float>(pbs[i], (const float*)ys[i], k, nl, nullptr, nullptr, nullptr, outs[i],
+                          iouts[i], oi, ws + offs[i], sizes[i], P.s[w], 1 + w);
+    if (r != GP_OK) return r;
+  }
+  for (int w = 0; w < nw; ++w) {
+    GP_CUDA_TRY(cudaEventRecord(P.join[w], P.s[w]));
+    GP_CUDA_TRY(cudaStreamWaitEvent(origin, P.join[w], 0));
+  }
+  return GP_OK;
+}
+
+// Instantiated batch graphs of this host thread, keyed by every argument that the
+// recorded work depends on (pointers, sizes, options).
+struct BatchGraph {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+};
+std::vector<BatchGraph>& batch_graphs() {
+  static thread_local std::vector<BatchGraph> cache;
+  return cache;
+}
+constexpr size_t kBatchGraphCache = 4;
+
+}  // namespace
+}  // namespace gp
+
+extern "C" size_t gp_workspace_size_batched(int32_t n_problems, const gp_problem* probs,
+                                            int32_t k, int32_t n_probes, int32_t max_iter) {
+  if (n_problems < 1 || !probs || n_probes < 0 || n_probes + 1 > kMaxT || max_iter < 1) return 0;
+  std::vector<Prob> pbs(n_problems);
+  for (int i = 0; i < n_problems; ++i) {
+    if (check_problem(&probs[i], false) != GP_OK) return 0;
+    pbs[i] = make_prob(&probs[i]);
+  }
+  return batch_layout(n_problems, pbs.data(), k, n_probes + 1, max_iter, nullptr, nullptr);
+}
+
+extern "C" gp_status gp_mll_and_grad_batched(int32_t n_problems, const gp_problem* probs,
+                                             const void* const* ys, int32_t k, int32_t n_probes,
+                                             double* const* outs, int32_t* const* iouts,
+                                             const gp_opts* opts, void* ws, size_t ws_bytes,
+                                             gp_stream_t stream) {
+  GP_REQUIRE(n_problems >= 1 && n_problems <= 4096, "n_problems=%d out of range [1, 4096]",
+             n_problems);
+  GP_REQUIRE(probs && ys && outs && iouts, "probs, ys, outs or iouts is NULL");
+  GP_TRY(check_opts(opts));
+  GP_REQUIRE(n_probes >= 0 && n_probes + 1 <= kMaxT, "n_probes=%d out of range", n_probes);
+  const int t = n_probes + 1;
+  std::vector<Prob> pbs(n_problems);
+  for (int i = 0; i < n_problems; ++i) {
+    gp_status r = check_problem(&probs[i]);
+    if (r != GP_OK) {
+      char msg[512];
+      snprintf(msg, sizeof(msg), "%s", last_error());
+      set_error("problem %d: %s", i, msg);
+      return r;
+    }
+    GP_REQUIRE(ys[i] && outs[i] && iouts[i], "problem %d: y, out or iout is NULL", i);
+    GP_REQUIRE(k >= 0 && k <= kMaxK && k <= probs[i].n,
+               "problem %d: k=%d out of range [0, min(n, %d)]", i, k, kMaxK);
+    pbs[i] = make_prob(&probs[i]);
+    GP_REQUIRE(!((pbs[i].prec == GP_BF16 || pbs[i].prec == GP_TF32) && !tc_supported(pbs[i], t)),
+               "problem %d: tensor-core precision does not support this shape", i);
+  }
+  std::vector<size_t> offs(n_problems), sizes(n_problems);
+  const size_t need = batch_layout(n_problems, pbs.data(), k, t, opts->max_iter, offs.data(),
+                                   sizes.data());
+  GP_TRY(check_ws(ws, ws_bytes, need));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* wsb = static_cast<char*>(ws);
+
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GP_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap == cudaStreamCaptureStatusActive)
+    return issue_batch(n_problems, pbs.data(), ys, k, n_probes, outs, iouts, *opts, wsb,
+                       offs.data(), sizes.data(), st);
+
+  // key of the recorded work
+  std::vector<uint64_t> key;
+  int dev = 0;
+  GP_CUDA_TRY(cudaGetDevice(&dev));
+  key.push_back((uint64_t)dev);
+  key.push_back((uint64_t)n_problems);
+  key.push_back((uint64_t)k);
+  key.push_back((uint64_t)n_probes);
+  key.push_back((uint64_t)reinterpret_cast<uintptr_t>(ws));
+  key.push_back((uint64_t)ws_bytes);
+  {
+    uint64_t ob[sizeof(gp_opts) / 8 + 1] = {};
+    memcpy(ob, opts, sizeof(gp_opts));
+    for (uint64_t v : ob) key.push_back(v);
+  }
+  for (int i = 0; i < n_problems; ++i) {
+    key.push_back((uint64_t)probs[i].n);
+    key.push_back(((uint64_t)(uint32_t)probs[i].d << 32) | (uint32_t)probs[i].kind);
+    key.push_back(((uint64_t)(uint32_t)probs[i].ard << 32) | (uint32_t)probs[i].precision);
+    key.push_back((uint64_t)reinterpret_cast<uintptr_t>(probs[i].X));
+    key.push_back((uint64_t)reinterpret_cast<uintptr_t>(probs[i].theta));
+    key.push_back((uint64_t)reinterpret_cast<uintptr_t>(ys[i]));
+    key.push_back((uint64_t)reinterpret_cast<uintptr_t>(outs[i]));
+    key.push_back((uint64_t)reinterpret_cast<uintptr_t>(iouts[i]));
+  }
+  std::vector<BatchGraph>& cache = batch_graphs();
+  for (BatchGraph& bg : cache)
+    if (bg.key == key) {
+      GP_CUDA_TRY(cudaGraphLaunch(bg.exec, st));
+      return GP_OK;
+    }
+
+  StreamPool& P = stream_pool();
+  if (!P.ok) {
+    set_error("could not create the batch streams");
+    return GP_ERR_CUDA;
+  }
+  GP_CUDA_TRY(cudaStreamBeginCapture(P.capture, cudaStreamCaptureModeRelaxed));
+  const gp_status r = issue_batch(n_problems, pbs.data(), ys, k, n_probes, outs, iouts, *opts,
+                                  wsb, offs.data(), sizes.data(), P.capture);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(P.capture, &graph);
+  if (r != GP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  GP_CUDA_TRY(ec);
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  GP_CUDA_TRY(ei);
+  if (cache.size() >= kBatchGraphCache) {
+    cudaGraphExecDestroy(cache.front().exec);
+    cache.erase(cache.begin());
+  }
+  cache.push_back(BatchGraph{key, exec});
+  GP_CUDA_TRY(cudaGraphLaunch(exec, st));
+  return GP_OK;
 }
 
 extern "C" gp_status gp_rademacher(uint64_t seed, int32_t stream_id, int64_t rows, int32_t cols,

@@ -12,6 +12,12 @@
 //
 // Every launch reads the device count of active columns and returns at once when
 // it is zero, so the host can enqueue several iterations between convergence polls.
+// When the stream is being captured into a CUDA graph, the iteration loop is a
+// conditional WHILE node instead: the body is one iteration, the kernels read the
+// iteration index and the residual-recompute flag from a device control block
+// (ctl), and a one-thread kernel at the end of the body advances it and sets the
+// loop condition (columns still active and j < max_iter).  Both paths launch the
+// same kernels in the same order, so they give identical results.
 // Column-wise reductions use per-block partials combined by the last block in
 // block order (deterministic).
 #include "ops.h"
@@ -29,6 +35,7 @@ struct Dev {
   double *rho, *rho0, *bnorm2, *alpha, *beta, *part, *S;
   int *active, *caps, *iters, *n_active, *status;
   unsigned* counter;
+  const int* ctl;   // null (host loop) or {j, recompute, recompute gate}
 };
 
 template <class T>
@@ -40,6 +47,7 @@ Dev<T> dev_of(const CgBufs<T>& cb, const T* B, int64_t ldb) {
   d.part = cb.part; d.S = cb.S;
   d.active = cb.active; d.caps = cb.caps; d.iters = cb.iters; d.n_active = cb.n_active;
   d.status = cb.status; d.counter = cb.counter;
+  d.ctl = nullptr;
   return d;
 }
 
@@ -340,6 +348,7 @@ __global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, int c0
 template <class T>
 __global__ void rho_combine(int t, int nb, int mode, int j, int max_iter, Dev<T> g) {
   if (*g.n_active == 0) return;
+  if (g.ctl && mode != 0) j = g.ctl[0];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = warp; c < t; c += blockDim.x >> 5) {
     if (!g.active[c]) continue;
@@ -382,6 +391,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) cg_alpha(int64_t n, int t, int j, int max_iter,
                                                     Dev<T> g) {
   if (*g.n_active == 0) return;
+  if (g.ctl) j = g.ctl[0];
   const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t r0, r1;
   row_chunk(n, &r0, &r1);
@@ -399,8 +409,14 @@ __global__ void __launch_bounds__(kThreads) cg_alpha(int64_t n, int t, int j, in
       if (lane != 0) continue;
       double al = g.rho[c] / pq;
       if (!(pq > 0.0) || !isfinite(al)) {
+        // breakdown: the operator is not positive definite in this precision (or
+        // the iterates overflowed); the column stops with the j steps it has
         *g.status = GP_ERR_NUMERIC;
-        al = 0.0;
+        g.alpha[(int64_t)c * max_iter + j] = 0.0;
+        g.active[c] = 0;
+        g.iters[c] = j;
+        atomicSub(g.n_active, 1);
+        continue;
       }
       g.alpha[(int64_t)c * max_iter + j] = al;
     }
@@ -442,6 +458,10 @@ __global__ void __launch_bounds__(kThreads) cg_update(int64_t n, int t, int j, i
                                                      double tol2, int use_caps, int recompute,
                                                      Dev<T> g) {
   if (*g.n_active == 0) return;
+  if (g.ctl) {
+    j = g.ctl[0];
+    recompute = g.ctl[1];
+  }
   const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t r0, r1;
   row_chunk(n, &r0, &r1);
@@ -470,6 +490,10 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) cg_resid(int64_t n, int t, int j, int max_iter,
                                                     double tol2, int use_caps, Dev<T> g) {
   if (*g.n_active == 0) return;
+  if (g.ctl) {
+    if (!g.ctl[1]) return;   // not a residual-recompute step
+    j = g.ctl[0];
+  }
   const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t r0, r1;
   row_chunk(n, &r0, &r1);
@@ -494,12 +518,33 @@ __global__ void __launch_bounds__(kThreads) cg_resid(int64_t n, int t, int j, in
 template <class T>
 __global__ void cg_pupdate(int64_t n, int t, int j, int max_iter, Dev<T> g) {
   if (*g.n_active == 0) return;
+  if (g.ctl) j = g.ctl[0];
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n * t) return;
   int c = (int)(e / n);
   if (!g.active[c]) return;
   const T be = (T)g.beta[(int64_t)c * max_iter + j];
   g.P[e] = fma(be, g.P[e], g.Z[e]);
+}
+
+// Device loop control: ctl = {j, recompute step?, recompute gate (= n_active on a
+// recompute step, else 0)}.  ctl_init sets j = 0; ctl_step advances j after an
+// iteration.  Both set the WHILE condition: some column active and j < max_iter.
+__device__ __forceinline__ void ctl_set(int* ctl, int j, int R, int max_iter, const int* n_active,
+                                        cudaGraphConditionalHandle h) {
+  const int rec = (R > 0 && (j + 1) % R == 0) ? 1 : 0;
+  ctl[0] = j;
+  ctl[1] = rec;
+  ctl[2] = rec ? *n_active : 0;
+  cudaGraphSetConditional(h, (*n_active > 0 && j < max_iter) ? 1u : 0u);
+}
+__global__ void ctl_init_kernel(int* ctl, int R, int max_iter, const int* n_active,
+                                cudaGraphConditionalHandle h) {
+  ctl_set(ctl, 0, R, max_iter, n_active, h);
+}
+__global__ void ctl_step_kernel(int* ctl, int R, int max_iter, const int* n_active,
+                                cudaGraphConditionalHandle h) {
+  ctl_set(ctl, ctl[0] + 1, R, max_iter, n_active, h);
 }
 
 // T_diag / T_off from the CG coefficients (Sec. S1.2).
@@ -539,6 +584,23 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(int64_t n, const T* a, co
       *out = r;
     }
   }
+}
+
+// A non-blocking stream per host thread and device on which the body of the
+// captured iteration loop is recorded (cudaStreamBeginCaptureToGraph).
+cudaStream_t capture_body_stream() {
+  struct BodyStream {
+    cudaStream_t s = nullptr;
+    int device = -1;
+  };
+  static thread_local BodyStream bs;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (bs.s == nullptr || bs.device != dev) {
+    if (cudaStreamCreateWithFlags(&bs.s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    bs.device = dev;
+  }
+  return bs.s;
 }
 
 int pick_tc16(int t) { return t <= 16 ? 16 : t <= 32 ? 32 : t <= 48 ? 48 : 64; }
@@ -608,6 +670,62 @@ gp_status cg_solve(const Prob& pb, MvmOp& mvm, const T* L, int64_t ldl, int k,
   GP_TRY(precond_apply<T>(n, t, L, ldl, k, Cinv, pb.theta, pb.D, 0, 0, o.max_iter, cb, g, nb, st));
   p_start<T><<<(unsigned)cdiv(n * t, 256), 256, 0, st>>>(n, t, g, PinvB, ldpb);
   GP_LAUNCH_CHECK();
+
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GP_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusActive) (void)capture_body_stream();   // create it early
+  if (cap == cudaStreamCaptureStatusActive) {
+    // graph capture: the iteration loop becomes a conditional WHILE node
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    GP_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cap, nullptr, &graph, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle h;
+    GP_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, graph, 0, 0));
+    ctl_init_kernel<<<1, 1, 0, st>>>(cb.ctl, R, o.max_iter, g.n_active, h);
+    GP_LAUNCH_CHECK();
+    GP_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cap, nullptr, &graph, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    GP_CUDA_TRY(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    GP_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies));
+    cudaStream_t bs = capture_body_stream();
+    if (!bs) return GP_ERR_CUDA;
+    GP_CUDA_TRY(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed));
+    Dev<T> gd = g;
+    gd.ctl = cb.ctl;
+    gp_status rs = GP_OK;
+    do {
+      rs = mvm.apply(gd.P, n, t, gd.Q, n, gd.n_active, bs);
+      if (rs != GP_OK) break;
+      cg_alpha<T><<<nb, kThreads, 0, bs>>>(n, t, 0, o.max_iter, gd);
+      cg_update<T><<<nb, kThreads, 0, bs>>>(n, t, 0, o.max_iter, tol2, use_caps, 0, gd);
+      if (R > 0) {
+        rs = mvm.apply(gd.X, n, t, gd.Q, n, cb.ctl + 2, bs);   // gated: recompute steps only
+        if (rs != GP_OK) break;
+        cg_resid<T><<<nb, kThreads, 0, bs>>>(n, t, 0, o.max_iter, tol2, use_caps, gd);
+      }
+      rs = precond_apply<T>(n, t, L, ldl, k, Cinv, pb.theta, pb.D, 1, 0, o.max_iter, cb, gd, nb,
+                            bs);
+      if (rs != GP_OK) break;
+      cg_pupdate<T><<<(unsigned)cdiv(n * t, 256), 256, 0, bs>>>(n, t, 0, o.max_iter, gd);
+      ctl_step_kernel<<<1, 1, 0, bs>>>(cb.ctl, R, o.max_iter, g.n_active, h);
+    } while (false);
+    cudaGraph_t body_out = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(bs, &body_out);
+    if (rs != GP_OK) return rs;
+    GP_CUDA_TRY(ec);
+    GP_LAUNCH_CHECK();
+    *host_status = 0;   // the status stays on the device (read after the graph runs)
+    return GP_OK;
+  }
 
   const bool timed = mvm_timing_enabled();
   for (int j = 0; j < o.max_iter; ++j) {

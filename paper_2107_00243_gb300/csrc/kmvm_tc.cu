@@ -21,6 +21,11 @@
 //          for the n = 1e5 RBF workload |E|_2 is a fraction of sigma^2, so CG stays on a
 //          positive-definite operator.  BF16 P (2^-8) is not enough: |E|_2 exceeds
 //          sigma^2 and CG breaks down (p^T K p <= 0).
+//   split mode (a device flag, read at launch): for smooth, ill-conditioned kernels
+//          (lambda_max(K) / sigma^2 large) even FP16 P can make K + sigma^2 I
+//          indefinite.  Then P is carried as FP16 P_hi + P_lo (22 bits) and GEMM2 adds
+//          P_lo V_hi (N = tp) into O columns [0, tp): 16 MMAs per tile, one 128-column
+//          P buffer instead of two of 64.
 //
 // Roles of a CTA (persistent over (row tile, column chunk) work units):
 //   warp 0      producer: bulk TMA copies (cp.async.bulk) of the pre-tiled A and B tiles
@@ -56,7 +61,8 @@ constexpr int kVWarp = 19;     // producer of the V ring
 constexpr long long kWaitNs = 2000000000LL;   // 2 s per drain wait before giving up
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s of SM clock per pipeline wait
 constexpr int kSBuf = 2;       // FP32 S buffers in TMEM (128 columns each)
-constexpr int kPBuf = 2;       // FP16 P buffers in TMEM (64 columns each)
+constexpr int kPBuf = 2;       // FP16 P buffers in TMEM (64 columns each; split mode: one
+                               // buffer of 128, P_hi then P_lo)
 constexpr int kEpiWarps = 16;
 
 // ---- PTX wrappers -------------------------------------------------------------------
@@ -249,7 +255,8 @@ struct TcArgs {
   int n, npad, ntiles, nchunks, tiles_per_chunk, kx, tp, t, kind, D;
   int nsb, nsv;              // shared-memory stages of the B and V rings (2 .. 4)
   const int* gate;
-  int* err;                  // err[0] = status, err[1] = where a wait gave up
+  int* err;                  // err[0] = status, err[1] = where a wait gave up,
+                             // err[2] = split mode (P as FP16 hi + lo) when nonzero
   float* dbg;                // optional: S of the first tile of unit 0
 };
 
@@ -290,13 +297,27 @@ __device__ __forceinline__ float kernel_from_s(float sv) {
   return (1.0f + ar + 1.6666666666666667f * r2) * ex2(-ar * L2E);
 }
 
-// P = k(S)/s for this thread's 32 S values, packed as 16 FP16 pairs.
+// P = k(S)/s for this thread's 32 S values, packed as 16 FP16 pairs; in split mode
+// also the FP16 residuals P - P_hi.
 template <int KIND>
-__device__ __forceinline__ void p_from_s(const uint32_t (&v)[32], uint32_t (&pk)[16]) {
+__device__ __forceinline__ void p_from_s(const uint32_t (&v)[32], uint32_t (&pk)[16],
+                                         uint32_t (&pl)[16], bool split) {
+  if (!split) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q)
-    pk[q] = pack_f16(kernel_from_s<KIND>(__uint_as_float(v[2 * q])),
-                     kernel_from_s<KIND>(__uint_as_float(v[2 * q + 1])));
+    for (int q = 0; q < 16; ++q)
+      pk[q] = pack_f16(kernel_from_s<KIND>(__uint_as_float(v[2 * q])),
+                       kernel_from_s<KIND>(__uint_as_float(v[2 * q + 1])));
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const float p0 = kernel_from_s<KIND>(__uint_as_float(v[2 * q]));
+    const float p1 = kernel_from_s<KIND>(__uint_as_float(v[2 * q + 1]));
+    const uint32_t h = pack_f16(p0, p1);
+    pk[q] = h;
+    const __half2 hh = *reinterpret_cast<const __half2*>(&h);
+    pl[q] = pack_f16(p0 - __low2float(hh), p1 - __high2float(hh));
+  }
 }
 
 
@@ -305,6 +326,8 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kx = g.kx, tp = g.tp, nsb = g.nsb, nsv = g.nsv;
+  const bool split = g.err[2] != 0;
+  const uint32_t npb = split ? 1u : (uint32_t)kPBuf;   // P buffers in the ring
   const uint32_t a_bytes = BM * kx * 2, b_bytes = BN * kx * 2;
   const uint32_t v_bytes = 2u * tp * BN * 2;   // FP16 hi and lo parts of V
   unsigned char* sA = smem;
@@ -472,6 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   } else if (warp == 2) {
     // ------------------------------------------------------------ GEMM2 issuer
     const uint32_t id2 = idesc_f16(BM, 2 * tp);   // B = [V_hi; V_lo], N = 2 tp
+    const uint32_t id2h = idesc_f16(BM, tp);      // B = V_hi only (split mode)
     const uint64_t dV0 = sdesc(smem_u32(sV), 128, BN * 16);
     const uint64_t v_step = v_bytes >> 4;
     uint32_t o_par = 0;
@@ -510,11 +534,16 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
 #pragma unroll
         for (int kk = 0; kk < BN / 16; ++kk)
           mma_ts(t_o, tpb + kk * 8, dv + (uint64_t)kk * 16, id2, (kk > 0) ? 1u : acc0);
+        if (split) {   // P_lo V_hi into O columns [0, tp)
+#pragma unroll
+          for (int kk = 0; kk < BN / 16; ++kk)
+            mma_ts(t_o, tpb + 64 + kk * 8, dv + (uint64_t)kk * 16, id2h, 1u);
+        }
         mma_commit(smem_u32(&bars->emptyV[st]));
         mma_commit(smem_u32(&bars->p_free[buf]));
         if (jj == nt - 1) mma_commit(smem_u32(&bars->o_full));
         sr.next(nsv);
-        br.next(kPBuf);
+        br.next(npb);
       }
       first_unit = false;
       if (!ok) break;
@@ -556,10 +585,10 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
           for (int q = 0; q < 32; ++q) g.dbg[row * BN + group * 32 + q] = __uint_as_float(v[q]);
         }
-        uint32_t pk[16];
-        if (g.kind == GP_RBF) p_from_s<GP_RBF>(v, pk);
-        else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v, pk);
-        else p_from_s<GP_MATERN52>(v, pk);
+        uint32_t pk[16], pl[16];
+        if (g.kind == GP_RBF) p_from_s<GP_RBF>(v, pk, pl, split);
+        else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v, pk, pl, split);
+        else p_from_s<GP_MATERN52>(v, pk, pl, split);
         // the P buffer is free once the GEMM2 that read it two tiles ago has completed
         if (!mbar_wait(smem_u32(&bars->p_free[pr.idx]), pr.phase ^ 1, abort, g.err, 33)) {
           ok = false;
@@ -567,12 +596,13 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         }
         tc_fence_after();
         GP_TMEM_ST16(tmem + 256 + pr.idx * 64 + lane_off + group * 16, pk);
+        if (split) GP_TMEM_ST16(tmem + 256 + 64 + lane_off + group * 16, pl);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bars->p_ready[pr.idx]));
         br.next(kSBuf);
-        pr.next(kPBuf);
+        pr.next(npb);
       }
       if (!ok) break;
       if (group != 0) continue;

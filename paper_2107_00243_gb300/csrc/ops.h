@@ -112,6 +112,7 @@ struct CgBufs {
   int* n_active;             // 1
   int* status;               // 1
   unsigned* counter;         // 1
+  int* ctl;                  // 4: device loop control (iteration j, recompute flag and gate)
 };
 constexpr int kCgBlocks = 304;
 size_t cg_atb_part_elems(int64_t n, int k, int t);

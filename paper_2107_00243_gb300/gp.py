@@ -46,7 +46,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("cg_tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("recompute_every", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("pivchol_tol", ctypes.c_double), ("check_every", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 _LIB = None
@@ -81,6 +81,8 @@ def load():
         "gp_rademacher": (i32, [ctypes.c_uint64, i32, i64, i32, vp, vp]),
         "gp_tc_exponent_tile": (i32, [P, vp, i64, i32, vp, i64, vp, vp, sz, vp]),
         "gp_kernel_mvm_noalloc": (i32, [P, vp, i64, i32, vp, i64, vp]),
+        "gp_workspace_size_batched": (sz, [i32, P, i32, i32, i32]),
+        "gp_mll_and_grad_batched": (i32, [i32, P, vp, i32, i32, vp, vp, O, vp, sz, vp]),
         "gp_launch_count": (i64, []),
         "gp_mvm_timing": (None, [i32]),
         "gp_mvm_timing_read": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
@@ -157,9 +159,13 @@ class Problem:
         return ctypes.byref(self._c)
 
 
-def opts(cg_tol=1e-6, max_iter=200, recompute_every=0, seed=0, pivchol_tol=0.0, check_every=0):
+OPT_SPLIT_P, OPT_AUTO_SPLIT = 1, 2
+
+
+def opts(cg_tol=1e-6, max_iter=200, recompute_every=0, seed=0, pivchol_tol=0.0, check_every=0,
+         flags=0):
     return _Opts(float(cg_tol), int(max_iter), int(recompute_every), int(seed),
-                 float(pivchol_tol), int(check_every), 0)
+                 float(pivchol_tol), int(check_every), int(flags))
 
 
 def gp_workspace_size(fn, n, d, k, t, precision, max_iter=1):
@@ -308,6 +314,63 @@ def gp_mll_and_grad(prob, y, k, n_probes, o, eps_override=None, piv_override=Non
                                     _ptr(io), _ptr(out), _ptr(iout), ctypes.byref(o), _ptr(ws),
                                     ws.numel(), _stream()))
     return st, out, iout
+
+
+def _problem_array(probs):
+    arr = (_Problem * len(probs))()
+    for i, pr in enumerate(probs):
+        pr.cref()                      # refresh the data pointers
+        arr[i] = pr._c
+    return arr
+
+
+def gp_workspace_size_batched(probs, k, n_probes, max_iter):
+    arr = _problem_array(probs)
+    return int(load().gp_workspace_size_batched(len(probs), arr, k, n_probes, max_iter))
+
+
+class Batch:
+    """Device buffers of one batched evaluation (gp_mll_and_grad_batched): the
+    problems, their targets, outputs and workspace, kept alive together so that the
+    library's cached CUDA graph for these pointers stays valid across calls."""
+
+    def __init__(self, probs, ys, k, n_probes, o):
+        self.probs, self.k, self.n_probes, self.o = list(probs), k, n_probes, o
+        t = n_probes + 1
+        self.ys = [torch.as_tensor(y).to(device=pr.device, dtype=pr.dtype).contiguous()
+                   for pr, y in zip(self.probs, ys)]
+        self.outs = [torch.zeros(out_len(pr.p, n_probes), dtype=torch.float64, device=pr.device)
+                     for pr in self.probs]
+        self.iouts = [torch.zeros(2 + t + max(k, 1), dtype=torch.int32, device=pr.device)
+                      for pr in self.probs]
+        nbytes = gp_workspace_size_batched(self.probs, k, n_probes, o.max_iter)
+        if nbytes == 0:
+            raise GPError("gp_workspace_size_batched", -1, "invalid batch")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.probs[0].device)
+        vp = ctypes.c_void_p
+        self._arr = _problem_array(self.probs)
+        self._ys = (vp * len(self.probs))(*[y.data_ptr() for y in self.ys])
+        self._outs = (vp * len(self.probs))(*[x.data_ptr() for x in self.outs])
+        self._iouts = (vp * len(self.probs))(*[x.data_ptr() for x in self.iouts])
+
+    def run(self):
+        """Launch the batch on the current stream (asynchronous); returns the status."""
+        return _check("gp_mll_and_grad_batched", load().gp_mll_and_grad_batched(
+            len(self.probs), self._arr, self._ys, self.k, self.n_probes, self._outs,
+            self._iouts, ctypes.byref(self.o), _ptr(self.ws), self.ws.numel(), _stream()))
+
+    def results(self):
+        """Host dicts (unpack) of every problem, after synchronising."""
+        torch.cuda.synchronize()
+        return [unpack(o, io, pr.p, self.n_probes, self.k)
+                for pr, o, io in zip(self.probs, self.outs, self.iouts)]
+
+
+def gp_mll_and_grad_batched(probs, ys, k, n_probes, o):
+    """One call of the batched estimator; returns the Batch (outputs in .outs/.iouts)."""
+    b = Batch(probs, ys, k, n_probes, o)
+    b.run()
+    return b
 
 
 def unpack(out, iout, p, n_probes, k):

@@ -61,3 +61,18 @@ def test_invalid_arguments_rejected_on_host(lib):
                                ctypes.byref(o), None, 0, None) == -1          # k > n
     assert lib.gp_pivchol(None, 2, 0.0, None, None, 10, None, None, None, 0, None) == -1
     assert lib.gp_rademacher(0, 3, 10, 1, 8, None) == -1
+
+
+def test_batched_workspace_size_is_sum_of_aligned_slices():
+    """Host-only query: one 256-byte aligned single-call workspace per problem."""
+    shapes = [(300, 4, gp.BF16), (1234, 8, gp.FP32), (4000, 12, gp.BF16)]
+    k, nl, mi = 20, 8, 300
+    want = 0
+    for n, d, prec in shapes:
+        sz = gp.gp_workspace_size(gp.FN_MLL_AND_GRAD, n, d, k, nl + 1, prec, mi)
+        want += (sz + 255) // 256 * 256
+    arr = (gp._Problem * len(shapes))(*[gp._Problem(n, d, gp.RBF, 0, prec, 0, 0)
+                                        for n, d, prec in shapes])
+    lib = gp.load()
+    assert lib.gp_workspace_size_batched(len(shapes), arr, k, nl, mi) == want
+    assert lib.gp_workspace_size_batched(0, arr, k, nl, mi) == 0

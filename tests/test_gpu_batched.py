@@ -1,0 +1,162 @@
+"""Graph capture and the batched estimator (gp_mll_and_grad_batched), through the C ABI.
+
+The captured form of an evaluation launches the same kernels in the same order as the
+eager form (mBCG's loop becomes a conditional WHILE node that stops on the same
+device-side decisions), and every reduction has a fixed order, so the two agree bit
+for bit.  The batched call gives each problem its own workspace slice and probe seed
+(opts.seed + i), so each of its results must equal that of a single call.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2107_00243_gb300 import gp, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2107_00243_gb300 import build
+    build.build()
+    gp.load()
+
+
+def _eager(prob, y, k, nl, o):
+    st, out, iout = gp.gp_mll_and_grad(prob, y, k, nl, o, workspace=gp.Workspace())
+    torch.cuda.synchronize()
+    return st, out.clone(), iout.clone()
+
+
+@pytest.mark.parametrize("precision", [gp.FP32, gp.BF16])
+def test_captured_evaluation_matches_eager(precision):
+    p = workloads.random_problem(1500, 6, kind=workloads.RBF, ard=True, seed=4, s2=0.02, k=30,
+                                 n_probes=8, tol=1e-3, max_iter=400, precision=precision)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, precision)
+    y = torch.as_tensor(p.y).to(device="cuda", dtype=prob.dtype)
+    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, recompute_every=10, seed=3)
+    st0, out0, iout0 = _eager(prob, y, p.k, p.n_probes, o)
+    assert st0 >= 0
+
+    ws = gp.Workspace()
+    out = torch.zeros_like(out0)
+    iout = torch.zeros_like(iout0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):                      # warm-up on the capture stream
+        gp.gp_mll_and_grad(prob, y, p.k, p.n_probes, o, workspace=ws, out=out, iout=iout)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        gp.gp_mll_and_grad(prob, y, p.k, p.n_probes, o, workspace=ws, out=out, iout=iout)
+    out.zero_()
+    iout.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(iout, iout0), (iout, iout0)
+    assert torch.equal(out, out0), (out - out0).abs().max()
+
+    # new hyperparameters in the same buffer: the replay equals a fresh eager call
+    theta2 = p.theta.copy()
+    theta2[0] *= 1.3
+    theta2[-1] *= 0.7
+    prob.set_theta(theta2)
+    g.replay()
+    torch.cuda.synchronize()
+    st2, out2, iout2 = _eager(prob, y, p.k, p.n_probes, o)
+    assert torch.equal(iout, iout2)
+    assert torch.equal(out, out2), (out - out2).abs().max()
+
+
+def _small_batch(n_problems=6, seed=0):
+    """C5-shaped problems (RBF isotropic, d in {4, 8, 12}, own lengthscale and noise)
+    at reduced sizes, in both tile precisions."""
+    ps = workloads.c5_batched(n_problems, seed=seed, n_lo=300, n_hi=4000)
+    precs = [gp.BF16 if i % 2 == 0 else gp.FP32 for i in range(n_problems)]
+    probs = [gp.Problem(p.X, p.theta, p.kind, p.ard, pr) for p, pr in zip(ps, precs)]
+    return ps, probs
+
+
+def test_batched_matches_single_calls():
+    ps, probs = _small_batch()
+    k, nl = 20, 8
+    f = gp.OPT_AUTO_SPLIT      # graph-recorded CG cannot be rerun by the host
+    o = gp.opts(cg_tol=1e-2, max_iter=500, recompute_every=25, seed=11, flags=f)
+    b = gp.Batch(probs, [p.y for p in ps], k, nl, o)
+    b.run()
+    res = b.results()
+    for i, (p, prob) in enumerate(zip(ps, probs)):
+        oi = gp.opts(cg_tol=1e-2, max_iter=500, recompute_every=25, seed=11 + i, flags=f)
+        st, out, iout = _eager(prob, b.ys[i], k, nl, oi)
+        assert st >= 0
+        assert res[i]["status"] == 0
+        assert torch.equal(b.iouts[i], iout), i
+        assert torch.equal(b.outs[i], out), (i, (b.outs[i] - out).abs().max())
+        assert np.isfinite(res[i]["mll"]) and np.all(np.isfinite(res[i]["grad"]))
+
+
+def test_batched_repeat_uses_new_values():
+    """A second launch of the same batch (the cached graph) after the hyperparameters
+    changed in place gives the results of fresh single calls at the new values."""
+    ps, probs = _small_batch(4, seed=5)
+    k, nl = 15, 6
+    f = gp.OPT_AUTO_SPLIT
+    o = gp.opts(cg_tol=1e-2, max_iter=500, recompute_every=25, seed=2, flags=f)
+    b = gp.Batch(probs, [p.y for p in ps], k, nl, o)
+    b.run()
+    first = [x.clone() for x in b.outs]
+    for prob, p in zip(probs, ps):
+        th = p.theta.copy()
+        th[0] *= 0.8
+        prob.set_theta(th)
+    b.run()
+    torch.cuda.synchronize()
+    for i, prob in enumerate(probs):
+        oi = gp.opts(cg_tol=1e-2, max_iter=500, recompute_every=25, seed=2 + i, flags=f)
+        _, out, iout = _eager(prob, b.ys[i], k, nl, oi)
+        assert torch.equal(b.outs[i], out), i
+        assert torch.equal(b.iouts[i], iout), i
+        assert not torch.equal(b.outs[i], first[i])
+
+
+def _ill_conditioned():
+    """A smooth, low-noise problem of the batched workload's family (d = 4, lengthscale
+    0.71, sigma^2 = 0.0082: lambda_max(K) / sigma^2 ~ 1.7e5) on which FP16 rounding of
+    k(r)/s makes K + sigma^2 I indefinite (checked densely on the CPU: lambda_min of the
+    rounded operator is -0.42 sigma^2)."""
+    return workloads.c5_batched(6, seed=0, n_lo=300, n_hi=4000)[4]
+
+
+def test_fast_mode_breakdown_reruns_in_split_mode():
+    p = _ill_conditioned()
+    k, nl = 20, 8
+    res = {}
+    for prec, flags in ((gp.BF16, 0), (gp.BF16, gp.OPT_SPLIT_P), (gp.BF16, gp.OPT_AUTO_SPLIT),
+                        (gp.FP32, 0)):
+        prob = gp.Problem(p.X, p.theta, p.kind, p.ard, prec)
+        o = gp.opts(cg_tol=1e-2, max_iter=1000, recompute_every=25, seed=1, flags=flags)
+        st, out, iout = _eager(prob, p.y, k, nl, o)
+        r = gp.unpack(out, iout, prob.p, nl, k)
+        assert st == 0 and r["status"] == 0, (prec, flags, st, r["status"])
+        assert np.all(r["iters"] < 1000)
+        res[(prec, flags)] = r
+    # the rerun is exactly the forced split-mode run, and so is the automatic choice
+    # (the Gershgorin bound flags this problem)
+    a, b, c = res[(gp.BF16, 0)], res[(gp.BF16, gp.OPT_SPLIT_P)], res[(gp.BF16, gp.OPT_AUTO_SPLIT)]
+    assert a["mll"] == b["mll"] == c["mll"]
+    ref = res[(gp.FP32, 0)]
+    assert abs(a["mll"] - ref["mll"]) <= 5e-3 * abs(ref["mll"])
+
+
+def test_batched_records_graph_with_ill_conditioned_member():
+    """The batch containing the problem above completes with every status 0 under
+    GP_OPT_AUTO_SPLIT."""
+    ps, probs = _small_batch()
+    k, nl = 20, 8
+    o = gp.opts(cg_tol=1e-2, max_iter=1000, recompute_every=25, seed=0, flags=gp.OPT_AUTO_SPLIT)
+    b = gp.Batch(probs, [p.y for p in ps], k, nl, o)
+    b.run()
+    for r in b.results():
+        assert r["status"] == 0 and np.isfinite(r["mll"])
