@@ -253,6 +253,78 @@ def run_case(args):
                       "ms": times}), flush=True)
 
 
+def run_batched(args):
+    """The batched workload: 64 independent RBF problems (n log-uniform in [2000,
+    50000], d in {4, 8, 12}, own lengthscale and noise; k = 50, l = 16, CG tol 1e-2,
+    BF16 tiles with the automatic split choice), one gp_mll_and_grad_batched call per
+    step (a cached CUDA graph after the first).  Launch configurations are autotuned
+    per shape first.  Reference point: the same 64 evaluations as eager single calls
+    one after another."""
+    import numpy as np
+    import torch
+    from paper_2107_00243_gb300 import build, gp, workloads
+    build.build()
+    gp.load()
+    ps = workloads.c5_batched(64, seed=0)
+    probs = [gp.Problem(p.X, p.theta, p.kind, p.ard, gp.BF16) for p in ps]
+    k, nl = ps[0].k, ps[0].n_probes
+    o = gp.opts(cg_tol=ps[0].tol, max_iter=ps[0].max_iter, recompute_every=25, seed=0,
+                flags=gp.OPT_AUTO_SPLIT)
+    tuned = {}
+    t0 = time.perf_counter()
+    for pr in probs:                                   # one tuning run per shape key
+        key = (pr.d, int(math.ceil(math.log2(max(pr.n / 128.0, 1.0)))))
+        if key not in tuned:
+            V = torch.randn(pr.n, nl + 1, device="cuda")
+            _, best = gp.gp_autotune(pr, V)
+            tuned[key] = best
+    tune_s = time.perf_counter() - t0
+    b = gp.Batch(probs, [p.y for p in ps], k, nl, o)
+    t0 = time.perf_counter()
+    b.run()                                            # records and instantiates the graph
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup - 1, 0)):
+        b.run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    res = b.results()
+    # the same evaluations as eager single calls, one after another
+    seq = 0.0
+    ws = gp.Workspace()
+    for i, (pr, y) in enumerate(zip(probs, b.ys)):
+        oi = gp.opts(cg_tol=o.cg_tol, max_iter=o.max_iter, recompute_every=25, seed=i,
+                     flags=gp.OPT_AUTO_SPLIT)
+        gp.gp_mll_and_grad(pr, y, k, nl, oi, workspace=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gp.gp_mll_and_grad(pr, y, k, nl, oi, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        seq += e0.elapsed_time(e1) / 1e3
+    value = statistics.median(times)
+    line = {"case": "batched", "metric": "s per batched MLL+grad step (64 problems)",
+            "value": value, "unit": "s", "higher_is_better": False, "steps": args.steps,
+            "warmup": args.warmup, "problems_per_s": 64.0 / value,
+            "sequential_single_calls_s": seq, "speedup_vs_sequential": seq / value,
+            "first_call_s_incl_capture": first_s, "autotune_s": tune_s,
+            "tuned_shapes": {f"d{d}_b{b_}": v for (d, b_), v in tuned.items()},
+            "n_range": [min(p.n for p in ps), max(p.n for p in ps)],
+            "statuses": sorted(set(r["status"] for r in res)),
+            "iters_max": int(max(int(r["iters"].max()) for r in res)),
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "rbf_batched64_n2e3-5e4_k50_l16_tol1e-2"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,12 +335,16 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=1,
                     help="timed steps of the plain FP32 form when --precision is mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg"], default="estimator",
+    ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg", "batched"],
+                    default="estimator",
                     help="kmvm / mbcg: time only the kernel product or a short CG call on a "
                          "smaller instance of the workload (for profiling)")
     ap.add_argument("--n", type=int, default=None, help="instance size for --case")
     ap.add_argument("--reps", type=int, default=3, help="calls for --case")
     args = ap.parse_args()
+    if args.case == "batched":
+        run_batched(args)
+        return
     if args.case != "estimator":
         run_case(args)
         return

@@ -236,7 +236,25 @@ gp_status gp_mll_and_grad_batched(int32_t n_problems, const gp_problem* probs,
                                   const gp_opts* opts, void* ws, size_t ws_bytes,
                                   gp_stream_t stream);
 
-/* Human-readable name of a status code (static storage). */
+/* Autotuner of the tensor-core product's launch configuration (GP_BF16): times the
+ * candidate column-chunk counts (work units per 128-row tile: 1..24, capped so every
+ * chunk keeps >= 4 tiles and the units stay <= ~16 per SM) and B / V shared-memory
+ * ring depths (4/4, 3/3, 2/2) on this problem with right-hand sides V (n x t,
+ * column-major, ld ldv), one warm-up and three timed products each, and records the
+ * fastest in a process-wide table keyed by (exponent operand width, t padded to 16,
+ * kernel kind, ceil(log2(n / 128))).  Every later product of a matching shape uses it;
+ * untuned shapes use the built-in heuristic.  W receives (K + sigma^2 I) V from the
+ * chosen configuration.  Workspace: that of GP_FN_KERNEL_MVM.  best (host, 4 int32,
+ * may be NULL): {chunks, B ring, V ring, candidates timed}.  Synchronises.  The
+ * paper has no counterpart (its products are whatever the GPU library picks).      */
+gp_status gp_autotune(const gp_problem* prob, const void* V, int64_t ldv, int32_t t,
+                      void* W, int64_t ldw, void* ws, size_t ws_bytes, gp_stream_t stream,
+                      int32_t* best);
+/* The launch configuration the product uses for this shape (host, 4 int32):
+ * {chunks, B ring, V ring, 1 if from the autotuner else 0}.  Host only.           */
+gp_status gp_tc_config(const gp_problem* prob, int32_t t, int32_t* config);
+
+/* Human-readable name of a status code (static storage). *//* Human-readable name of a status code (static storage). */
 const char* gp_status_string(int32_t status);
 
 /* Detail of the last host-side validation failure on this thread (static storage). */

@@ -596,6 +596,45 @@ extern "C" gp_status gp_kernel_mvm(const gp_problem* prob, const void* V, int64_
   return run_kernel_mvm<float>(pb, V, ldv, t, W, ldw, P, st);
 }
 
+extern "C" gp_status gp_autotune(const gp_problem* prob, const void* V, int64_t ldv, int32_t t,
+                                 void* W, int64_t ldw, void* ws, size_t ws_bytes,
+                                 gp_stream_t stream, int32_t* best) {
+  GP_TRY(check_problem(prob));
+  GP_REQUIRE(t >= 1 && t <= kMaxT, "t=%d out of range [1, %d]", t, kMaxT);
+  GP_REQUIRE(V && W, "V or W is NULL");
+  GP_REQUIRE(ldv >= prob->n && ldw >= prob->n, "leading dimensions must be >= n");
+  GP_REQUIRE(V != W, "W must not alias V");
+  Prob pb = make_prob(prob);
+  GP_REQUIRE(pb.prec == GP_BF16 && tc_supported(pb, t),
+             "autotuning applies to the tensor-core product (GP_BF16, t <= 64)");
+  GP_TRY(check_ws(ws, ws_bytes, gp_workspace_size(GP_FN_KERNEL_MVM, pb.n, pb.d, 0, t, pb.prec, 1)));
+  Arena A;
+  A.base = static_cast<char*>(ws);
+  MvmPlan P;
+  plan_mvm(A, pb, t, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  GP_TRY(run_prep<float>(pb, P.prep, st));
+  GP_CUDA_TRY(cudaMemsetAsync(P.tc.err, 0, kTcErrInts * sizeof(int), st));
+  GP_TRY(tc_prepare_inputs(pb, P.prep.pr.Xs, P.tc, st));
+  int b4[4] = {0, 0, 0, 0};
+  GP_TRY(tc_autotune(pb, P.tc, static_cast<const float*>(V), ldv, t, static_cast<float*>(W), ldw,
+                     st, b4));
+  if (best)
+    for (int i = 0; i < 4; ++i) best[i] = b4[i];
+  return GP_OK;
+}
+
+extern "C" gp_status gp_tc_config(const gp_problem* prob, int32_t t, int32_t* config) {
+  GP_TRY(check_problem(prob, false));
+  GP_REQUIRE(t >= 1 && t <= kMaxT, "t=%d out of range [1, %d]", t, kMaxT);
+  GP_REQUIRE(config, "config is NULL");
+  Prob pb = make_prob(prob);
+  int c4[4];
+  tc_config(pb, t, c4);
+  for (int i = 0; i < 4; ++i) config[i] = c4[i];
+  return GP_OK;
+}
+
 extern "C" gp_status gp_kernel_grad_mvm(const gp_problem* prob, const void* V, int64_t ldv,
                                         int32_t t, void* dW, int64_t ldw, void* ws,
                                         size_t ws_bytes, gp_stream_t stream) {

@@ -49,6 +49,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <map>
+#include <mutex>
+#include <vector>
+
 namespace gp {
 namespace {
 
@@ -787,6 +791,34 @@ int nchunks_for(int ntiles) {
   int maxc = std::max(1, ntiles / 16);
   return std::max(1, std::min(want, maxc));
 }
+// Largest column-chunk count the autotuner may pick (the partial-sum buffer is sized
+// for it): chunks of at least 4 tiles, and no more than ~16 work units per SM.
+int max_chunks_for(int ntiles) {
+  const int a = std::max(1, std::min(ntiles / 4, (int)cdiv(16LL * 152, ntiles)));
+  return std::max(a, nchunks_for(ntiles));
+}
+
+// ---- autotuned launch configurations ----------------------------------------------------
+// Key: exponent operand width kx, padded t, kernel kind, split mode and the tile-count
+// bucket ceil(log2(ntiles)); value: column chunks and the B / V ring depths.
+struct TcConfig {
+  int nchunks = 0, nsb = 0, nsv = 0;
+};
+std::mutex g_tune_mu;
+std::map<uint64_t, TcConfig> g_tune;
+uint64_t tune_key(int kx, int tp, int kind, int split, int ntiles) {
+  int b = 0;
+  while ((1 << b) < ntiles) ++b;
+  return ((uint64_t)kx << 40) | ((uint64_t)tp << 32) | ((uint64_t)kind << 24) |
+         ((uint64_t)(split ? 1 : 0) << 16) | (uint64_t)b;
+}
+bool tune_lookup(uint64_t key, TcConfig* c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *c = it->second;
+  return true;
+}
 constexpr size_t kSmemCap = 220 * 1024;
 size_t smem_bytes(int kx, int tp, int nsb, int nsv) {
   size_t b = (size_t)BM * kx * 2 + (size_t)nsb * BN * kx * 2 + (size_t)nsv * tp * BN * 2 * 2 +
@@ -819,7 +851,7 @@ size_t tc_vpack_bytes(int64_t n, int t, int prec) {
 }
 size_t tc_part_elems(int64_t n, int t) {
   const int nt = ntiles_for(n);
-  return (size_t)nchunks_for(nt) * tp_for(t) * nt * BM;
+  return (size_t)max_chunks_for(nt) * tp_for(t) * nt * BM;
 }
 bool tc_supported(const Prob& pb, int t) {
   return pb.prec == GP_BF16 && t >= 1 && t <= 64 && pb.d <= kMaxD;
@@ -841,11 +873,13 @@ gp_status kmvm_tc(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv,
   return kmvm_tc_debug(pb, tb, V, ldv, t, W, ldw, gate, nullptr, st);
 }
 
-gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
-                        float* W, int64_t ldw, const int* gate, float* dbg, cudaStream_t st) {
+namespace {
+gp_status kmvm_tc_cfg(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
+                      float* W, int64_t ldw, const int* gate, float* dbg, const TcConfig* cfg,
+                      cudaStream_t st) {
   const int n = (int)pb.n;
   const int nt = ntiles_for(pb.n), kx = kx_for(pb.d), tp = tp_for(t);
-  const int nch = nchunks_for(nt);
+  const int nch = cfg ? std::min(cfg->nchunks, max_chunks_for(nt)) : nchunks_for(nt);
   const int npad = nt * BM;
   __nv_bfloat16* xa = static_cast<__nv_bfloat16*>(tb.xpack);
   __nv_bfloat16* xb = xa + (size_t)nt * BM * kx;
@@ -874,6 +908,10 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
   a.kind = pb.kind;
   a.D = pb.D;
   stages_for(kx, tp, &a.nsb, &a.nsv);
+  if (cfg && cfg->nsb >= 2 && cfg->nsv >= 2 && smem_bytes(kx, tp, cfg->nsb, cfg->nsv) <= kSmemCap) {
+    a.nsb = cfg->nsb;
+    a.nsv = cfg->nsv;
+  }
   a.gate = gate;
   a.err = err;
   a.dbg = dbg;
@@ -894,6 +932,84 @@ gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_
       n, npad, t, tp, a.nchunks, tb.part, V, ldv, pb.theta, pb.D, tb.vscale, W, ldw, gate, err);
   GP_LAUNCH_CHECK();
   return GP_OK;
+}
+}  // namespace
+
+gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
+                        float* W, int64_t ldw, const int* gate, float* dbg, cudaStream_t st) {
+  // the split flag is on the device; the tuned table is keyed on fast mode, which is
+  // what the tuner times (split mode has the same tiling and ring structure)
+  TcConfig c;
+  const bool tuned = tune_lookup(tune_key(kx_for(pb.d), tp_for(t), pb.kind, 0, ntiles_for(pb.n)), &c);
+  return kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, gate, dbg, tuned ? &c : nullptr, st);
+}
+
+// Times the candidate configurations for this problem shape (one warm-up and three
+// timed products each, CUDA events on `st`), records the fastest in the table and
+// leaves its product in W.  Synchronises with `st`.
+gp_status tc_autotune(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
+                      float* W, int64_t ldw, cudaStream_t st, int* best_out) {
+  const int nt = ntiles_for(pb.n), kx = kx_for(pb.d), tp = tp_for(t);
+  std::vector<TcConfig> cands;
+  const int rings[3][2] = {{kMaxStages, kMaxStages}, {3, 3}, {2, 2}};
+  const int chunk_opts[] = {1, 2, 3, 4, 6, 8, 12, 16, 24};
+  for (int c : chunk_opts) {
+    if (c > max_chunks_for(nt)) break;
+    for (auto& r : rings)
+      if (smem_bytes(kx, tp, r[0], r[1]) <= kSmemCap) cands.push_back(TcConfig{c, r[0], r[1]});
+  }
+  cudaEvent_t e0, e1;
+  GP_CUDA_TRY(cudaEventCreate(&e0));
+  GP_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  TcConfig bc;
+  gp_status rs = GP_OK;
+  for (const TcConfig& c : cands) {
+    rs = kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &c, st);
+    if (rs != GP_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && rs == GP_OK; ++r)
+      rs = kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &c, st);
+    cudaEventRecord(e1, st);
+    if (rs != GP_OK) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rs = GP_ERR_CUDA;
+      break;
+    }
+    if (ms < best) {
+      best = ms;
+      bc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rs != GP_OK) return rs;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(kx, tp, pb.kind, 0, nt)] = bc;
+  }
+  if (best_out) {
+    best_out[0] = bc.nchunks;
+    best_out[1] = bc.nsb;
+    best_out[2] = bc.nsv;
+    best_out[3] = (int)cands.size();
+  }
+  // W from the chosen configuration
+  return kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &bc, st);
+}
+
+// The configuration the product uses for this shape: {nchunks, nsb, nsv, tuned}.
+void tc_config(const Prob& pb, int t, int* out4) {
+  const int nt = ntiles_for(pb.n), kx = kx_for(pb.d), tp = tp_for(t);
+  TcConfig c;
+  const bool tuned = tune_lookup(tune_key(kx, tp, pb.kind, 0, nt), &c);
+  int nsb, nsv;
+  stages_for(kx, tp, &nsb, &nsv);
+  out4[0] = tuned ? std::min(c.nchunks, max_chunks_for(nt)) : nchunks_for(nt);
+  out4[1] = tuned ? c.nsb : nsb;
+  out4[2] = tuned ? c.nsv : nsv;
+  out4[3] = tuned ? 1 : 0;
 }
 
 }  // namespace gp

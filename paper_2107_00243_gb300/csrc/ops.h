@@ -56,6 +56,11 @@ gp_status tc_prepare_inputs(const Prob& pb, const void* Xs, const TcBufs& tb, cu
 gp_status kmvm_tc(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
                   float* W, int64_t ldw, const int* gate, cudaStream_t st);
 // Same, and (dbg != null) the exponent tile S of the first tile pair -> dbg (128 x 128).
+// Autotuner of the TC launch configuration (column chunks, ring depths) for this
+// shape; best_out (may be null) = {nchunks, nsb, nsv, candidates timed}.
+gp_status tc_autotune(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
+                      float* W, int64_t ldw, cudaStream_t st, int* best_out);
+void tc_config(const Prob& pb, int t, int* out4);
 gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
                         float* W, int64_t ldw, const int* gate, float* dbg, cudaStream_t st);
 

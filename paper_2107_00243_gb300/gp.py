@@ -82,6 +82,8 @@ def load():
         "gp_tc_exponent_tile": (i32, [P, vp, i64, i32, vp, i64, vp, vp, sz, vp]),
         "gp_kernel_mvm_noalloc": (i32, [P, vp, i64, i32, vp, i64, vp]),
         "gp_workspace_size_batched": (sz, [i32, P, i32, i32, i32]),
+        "gp_autotune": (i32, [P, vp, i64, i32, vp, i64, vp, sz, vp, vp]),
+        "gp_tc_config": (i32, [P, i32, vp]),
         "gp_mll_and_grad_batched": (i32, [i32, P, vp, i32, i32, vp, vp, O, vp, sz, vp]),
         "gp_launch_count": (i64, []),
         "gp_mvm_timing": (None, [i32]),
@@ -314,6 +316,29 @@ def gp_mll_and_grad(prob, y, k, n_probes, o, eps_override=None, piv_override=Non
                                     _ptr(io), _ptr(out), _ptr(iout), ctypes.byref(o), _ptr(ws),
                                     ws.numel(), _stream()))
     return st, out, iout
+
+
+def gp_autotune(prob, V, workspace=None):
+    """Tune the tensor-core product's launch configuration for this shape; returns
+    (W, {chunks, b_ring, v_ring, candidates})."""
+    lib = load()
+    Vc = _colmajor(V, prob.dtype, prob.device)
+    t = Vc.shape[0]
+    W = torch.empty_like(Vc)
+    ws = (workspace or _WS).get(gp_workspace_size(FN_KERNEL_MVM, prob.n, prob.d, 0, t,
+                                                  prob.precision), prob.device)
+    best = (ctypes.c_int32 * 4)()
+    _check("gp_autotune", lib.gp_autotune(prob.cref(), _ptr(Vc), prob.n, t, _ptr(W), prob.n,
+                                          _ptr(ws), ws.numel(), _stream(),
+                                          ctypes.cast(best, ctypes.c_void_p)))
+    return W.t(), {"chunks": best[0], "b_ring": best[1], "v_ring": best[2],
+                   "candidates": best[3]}
+
+
+def gp_tc_config(prob, t):
+    c = (ctypes.c_int32 * 4)()
+    _check("gp_tc_config", load().gp_tc_config(prob.cref(), t, ctypes.cast(c, ctypes.c_void_p)))
+    return {"chunks": c[0], "b_ring": c[1], "v_ring": c[2], "tuned": bool(c[3])}
 
 
 def _problem_array(probs):

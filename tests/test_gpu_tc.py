@@ -133,3 +133,24 @@ def test_estimator_bf16_full_size():
         res[prec] = r
     a, b = res[gp.BF16], res[gp.FP32]
     assert abs(a["mll"] - b["mll"]) <= 5e-3 * abs(b["mll"])
+
+
+def test_autotune_records_config_and_keeps_product():
+    """The tuner times its candidates, records the fastest for this shape, and the
+    product stays within the same bound under the tuned configuration."""
+    n, d, t = 3000, 8, 17
+    p = _problem(n, d, kernels.RBF, True, seed=13)
+    prob = gp.Problem(p.X, p.theta, p.kind, True, gp.BF16)
+    V = np.random.default_rng(2).standard_normal((n, t))
+    W, best = gp.gp_autotune(prob, torch.from_numpy(V))
+    assert best["candidates"] >= 3 and best["chunks"] >= 1
+    cfg = gp.gp_tc_config(prob, t)
+    assert cfg["tuned"]
+    assert (cfg["chunks"], cfg["b_ring"], cfg["v_ring"]) == (best["chunks"], best["b_ring"],
+                                                            best["v_ring"])
+    op = kernels.KernelOperator(p.kind, p.X, p.theta, True)
+    K = kernels.kernel_block(p.kind, p.X, p.X, p.theta, True)
+    ref = op.matvec(V)
+    bound = 2.0 ** -10 * (np.abs(K) @ np.abs(V)) + 1e-6
+    for got in (W.cpu().numpy(), gp.gp_kernel_mvm(prob, torch.from_numpy(V)).cpu().numpy()):
+        assert (np.abs(got - ref) / bound).max() <= 1.0
