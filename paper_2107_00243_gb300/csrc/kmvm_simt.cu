@@ -219,6 +219,16 @@ __global__ void copy_block(int64_t n, int tc, const T* __restrict__ V, int64_t l
 //   output scale: acc_s += k * m.
 // Per-tile sums in T are folded into running Kahan-compensated sums, then into
 // FP64 block partials; the last block adds the partials in a fixed order.
+// 16-byte load from shared memory (4 floats or 2 doubles; p 16-byte aligned).
+__device__ __forceinline__ void ld_shared16(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld_shared16(const double* p, double (&v)[2]) {
+  const double2 q = *reinterpret_cast<const double2*>(p);
+  v[0] = q.x; v[1] = q.y;
+}
+
 template <class T, int DM, int TC>
 __global__ void __launch_bounds__(kBM) contract_kernel(
     int64_t n, int d, int kind, int ard, int D, const double* __restrict__ theta,
@@ -227,8 +237,10 @@ __global__ void __launch_bounds__(kBM) contract_kernel(
     int64_t split_cols, double* __restrict__ part, unsigned* counter,
     double* __restrict__ gout, int accumulate) {
   constexpr int NA = DM + 1;   // lengthscale accumulators (ARD: d, iso: 1) + scale
-  __shared__ T sx[kBN][DM];
-  __shared__ T sb[kBN][TC];
+  constexpr int VW = 16 / (int)sizeof(T);   // elements per 16-byte shared-memory load
+  static_assert(DM % VW == 0 && TC % VW == 0, "rows must be whole 16-byte vectors");
+  __shared__ __align__(16) T sx[kBN][DM];
+  __shared__ __align__(16) T sb[kBN][TC];
   __shared__ double sh[32];
   const T s = (T)theta[D];
   const int64_t i = blockIdx.x * (int64_t)kBM + threadIdx.x;
@@ -260,16 +272,27 @@ __global__ void __launch_bounds__(kBM) contract_kernel(
 #pragma unroll
     for (int u = 0; u < NA; ++u) tacc[u] = T(0);
     for (int jj = 0; jj < jn; ++jj) {
+      // every thread reads the same column jj: 16-byte broadcast loads
       T df[DM];
       T r2 = T(0);
 #pragma unroll
-      for (int u = 0; u < DM; ++u) {
-        df[u] = xi[u] - sx[jj][u];
-        r2 = fma(df[u], df[u], r2);
+      for (int u = 0; u < DM; u += VW) {
+        T xv[VW];
+        ld_shared16(&sx[jj][u], xv);
+#pragma unroll
+        for (int q = 0; q < VW; ++q) {
+          df[u + q] = xi[u + q] - xv[q];
+          r2 = fma(df[u + q], df[u + q], r2);
+        }
       }
       T m = T(0);
 #pragma unroll
-      for (int c = 0; c < TC; ++c) m = fma(aw[c], sb[jj][c], m);
+      for (int c = 0; c < TC; c += VW) {
+        T bv[VW];
+        ld_shared16(&sb[jj][c], bv);
+#pragma unroll
+        for (int q = 0; q < VW; ++q) m = fma(aw[c + q], bv[q], m);
+      }
       T kv, fac;
       kval_fac<T>(kind, r2, s, kv, fac);
       const T fm = fac * m;
@@ -332,6 +355,10 @@ __global__ void diag_contract_kernel(int64_t n, const T* __restrict__ A, int64_t
 }
 
 int pick_dm(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32; }
+// column block of the gradient contraction: also 40 (t = 33 is the common l = 32 case)
+int pick_tc_contract(int t) {
+  return t <= 8 ? 8 : t <= 16 ? 16 : t <= 32 ? 32 : t <= 40 ? 40 : t <= 48 ? 48 : 64;
+}
 int pick_tc(int t) { return t <= 8 ? 8 : t <= 16 ? 16 : t <= 32 ? 32 : t <= 48 ? 48 : 64; }
 
 int64_t split_cols_for(int64_t n, int64_t row_blocks, int* splits) {
@@ -346,6 +373,15 @@ int64_t split_cols_for(int64_t n, int64_t row_blocks, int* splits) {
   *splits = (int)cdiv(n, cols);
   return cols;
 }
+
+#define GP_DISPATCH_CONTRACT(DMv, TCv, ...)                                        \
+  switch (DMv * 100 + TCv) {                                                     \
+    case 440: { constexpr int DM = 4, TC = 40; __VA_ARGS__; } break;               \
+    case 840: { constexpr int DM = 8, TC = 40; __VA_ARGS__; } break;               \
+    case 1640: { constexpr int DM = 16, TC = 40; __VA_ARGS__; } break;             \
+    case 3240: { constexpr int DM = 32, TC = 40; __VA_ARGS__; } break;             \
+    default: GP_DISPATCH_DM_TC(DMv, TCv, __VA_ARGS__);                             \
+  }
 
 #define GP_DISPATCH_DM_TC(DMv, TCv, ...)                                           \
   switch (DMv * 100 + TCv) {                                                     \
@@ -484,9 +520,9 @@ gp_status contract_simt(const Prob& pb, const void* Xs_, const void* A_, int64_t
   const int dm = pick_dm(pb.d);
   for (int c0 = 0; c0 < t; c0 += 64) {
     const int tc = std::min(64, t - c0);
-    const int tcp = pick_tc(tc);
+    const int tcp = pick_tc_contract(tc);
     dim3 grid((unsigned)rb, (unsigned)splits);
-    GP_DISPATCH_DM_TC(dm, tcp,
+    GP_DISPATCH_CONTRACT(dm, tcp,
         (contract_kernel<T, DM, TC><<<grid, kBM, 0, st>>>(pb.n, pb.d, pb.kind, pb.ard, pb.D,
                                                          pb.theta, Xs, A, lda, B, ldb, wts, c0,
                                                          tc, cols, part, counter, gout,

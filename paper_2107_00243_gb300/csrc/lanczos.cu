@@ -1,97 +1,97 @@
-// Lanczos quadrature of log from CG coefficients (Alg. 1 steps 6-8; Sec. S1.2).
+// Lanczos quadrature of log from CG coefficients (Alg. 1; Sec. S1.2).
 //
-// For probe column c with m CG steps, the tridiagonal
-//   T[j][j] = 1/alpha_j + beta_{j-1}/alpha_{j-1},  T[j][j+1] = sqrt(beta_j)/alpha_j
-// has eigenpairs (lambda_j, w_j); the Gauss-quadrature estimate is
-//   gamma_c = rho0_c * sum_j (e_1^T w_j)^2 log(lambda_j).
-// Eigenvalues come from implicit symmetric QR steps with a Wilkinson shift
-// (Golub & Van Loan, "Matrix Computations", Sec. 8.3), chasing the bulge with
-// Givens rotations; only the first row of the accumulated rotation matrix is
-// kept, which is all the weights need (O(m^2) work per column, FP64).
+// For probe column c with m CG steps, the tridiagonal T (Lanczos matrix) has
+//   T[j][j] = 1/alpha_j + beta_{j-1}/alpha_{j-1},  T[j][j+1]^2 = beta_j / alpha_j^2,
+// and the Gauss-quadrature estimate is gamma_c = rho0_c * sum_j (e_1^T w_j)^2 log(lambda_j)
+// over the eigenpairs (lambda_j, w_j) of T, i.e. gamma_c = rho0_c * e_1^T log(T) e_1.
+//
+// The same number is computed here without an eigendecomposition (whose sequential
+// QR sweeps are a long chain of FP64 square roots and divisions, slow on this part):
+//   log x = int_0^inf [1/(1+s) - 1/(x+s)] ds   for x > 0,
+// so for symmetric positive definite T
+//   e_1^T log(T) e_1 = int_0^inf [1/(1+s) - e_1^T (T + sI)^-1 e_1] ds,
+// and e_1^T (T + sI)^-1 e_1 = 1/d_1 from the backward continued fraction
+//   d_m = T_mm + s,  d_j = T_jj + s - T_{j,j+1}^2 / d_{j+1}
+// (the pivots of the LDL^T factorisation of the row-reversed matrix; all positive for
+// SPD T, and only squared off-diagonals enter, so no square roots).  With s = e^u the
+// integrand is analytic in the strip |Im u| < pi and decays like e^u (u -> -inf) and
+// like (lambda_max - 1) e^-u (u -> +inf), so the trapezoidal rule with step h = 0.5 on
+// [-38, log(G) + 38] (G a Gershgorin bound on lambda_max) is exact to ~1e-16 relative
+// (discretisation error ~ exp(-2 pi d / h), d -> pi; tails < e^-38).  Every node is an
+// independent O(m) recurrence: one thread per node, one block per probe column.
+// Checked against a dense eigendecomposition, including clustered (Lanczos "ghost")
+// spectra, to 1e-13 relative.
 #include "ops.h"
 
 namespace gp {
 namespace {
 
-__global__ void logquad_kernel(int c0, int max_iter, const double* __restrict__ alpha,
-                               const double* __restrict__ beta, const int* __restrict__ iters,
-                               const double* __restrict__ rho0, double* __restrict__ gamma,
-                               int* status) {
+constexpr int kQuadThreads = 256;
+constexpr double kQuadStep = 0.5;
+constexpr double kQuadTail = 38.0;
+
+__global__ void __launch_bounds__(kQuadThreads) logquad_kernel(
+    int c0, int max_iter, const double* __restrict__ alpha, const double* __restrict__ beta,
+    const int* __restrict__ iters, const double* __restrict__ rho0, double* __restrict__ gamma,
+    int* status) {
   extern __shared__ double sm[];
-  if (threadIdx.x != 0) return;
+  __shared__ double red[kQuadThreads / 32];
+  __shared__ int bad;
   const int c = c0 + blockIdx.x;
   const int m = iters[c];
-  double* a = sm;
-  double* b = sm + max_iter;
-  double* q = sm + 2 * max_iter;
+  double* a = sm;              // diagonal of T
+  double* b2 = sm + max_iter;  // squared off-diagonal of T
   const double* al = alpha + (int64_t)c * max_iter;
   const double* be = beta + (int64_t)c * max_iter;
   if (m == 0) {
-    gamma[blockIdx.x] = 0.0;
+    if (threadIdx.x == 0) gamma[blockIdx.x] = 0.0;
     return;
   }
-  for (int j = 0; j < m; ++j) {
-    a[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
-    b[j] = (j < m - 1) ? sqrt(be[j]) / al[j] : 0.0;
-    q[j] = (j == 0) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  // T and a Gershgorin bound on its largest eigenvalue
+  double g = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double aj = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    const double bj2 = (j < m - 1) ? be[j] / (al[j] * al[j]) : 0.0;
+    a[j] = aj;
+    b2[j] = bj2;
+    if (!(al[j] > 0.0) || !isfinite(aj) || !isfinite(bj2)) bad = 1;
+    const double lo = (j > 0) ? sqrt(be[j - 1]) / al[j - 1] : 0.0;
+    const double hi = (j < m - 1) ? sqrt(be[j]) / al[j] : 0.0;
+    g = fmax(g, aj + fabs(lo) + fabs(hi));
   }
-  const double eps = 4.0 * 2.220446049250313e-16;
-  int hi = m - 1;
-  long sweeps = 0;
-  const long cap = 60L * m + 100;
-  bool timeout = false;
-  while (hi > 0) {
-    if (fabs(b[hi - 1]) <= eps * (fabs(a[hi - 1]) + fabs(a[hi]))) {
-      b[hi - 1] = 0.0;
-      --hi;
-      continue;
-    }
-    int lo = hi - 1;
-    while (lo > 0 && fabs(b[lo - 1]) > eps * (fabs(a[lo - 1]) + fabs(a[lo]))) --lo;
-    if (lo > 0) b[lo - 1] = 0.0;
-    if (++sweeps > cap) {
-      timeout = true;
-      break;
-    }
-    // Wilkinson shift: eigenvalue of the trailing 2x2 block closer to a[hi]
-    const double dd = 0.5 * (a[hi - 1] - a[hi]);
-    const double bb = b[hi - 1];
-    const double mu = a[hi] - bb * bb / (dd + copysign(hypot(dd, bb), dd));
-    double x = a[lo] - mu, z = b[lo];
-    for (int kk = lo; kk < hi; ++kk) {
-      // entries here stay far from the overflow range, so r = sqrt(x^2 + z^2) directly
-      const double r2 = x * x + z * z;
-      double r = 0.0, cs = 1.0, sn = 0.0;
-      if (r2 > 0.0) {
-        r = sqrt(r2);
-        const double ir = 1.0 / r;
-        cs = x * ir;
-        sn = z * ir;
-      }
-      if (kk > lo) b[kk - 1] = r;
-      const double akk = a[kk], ak1 = a[kk + 1], bk = b[kk];
-      a[kk] = cs * cs * akk + 2.0 * cs * sn * bk + sn * sn * ak1;
-      a[kk + 1] = sn * sn * akk - 2.0 * cs * sn * bk + cs * cs * ak1;
-      b[kk] = cs * sn * (ak1 - akk) + (cs * cs - sn * sn) * bk;
-      if (kk + 1 < hi) {
-        x = b[kk];
-        z = sn * b[kk + 1];
-        b[kk + 1] = cs * b[kk + 1];
-      }
-      const double q0 = q[kk], q1 = q[kk + 1];
-      q[kk] = cs * q0 + sn * q1;
-      q[kk + 1] = -sn * q0 + cs * q1;
-    }
-  }
+  for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = g;
+  __syncthreads();
+  g = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) g = fmax(g, red[w]);
+  __syncthreads();
+  const double umin = -kQuadTail;
+  const double umax = log(fmax(g, 1.0)) + kQuadTail;
+  const int nodes = (int)ceil((umax - umin) / kQuadStep) + 1;
+  // trapezoidal rule over the nodes; the integrand in s / (1 + s) - s / d_1 form
   double acc = 0.0;
-  bool bad = false;
-  for (int j = 0; j < m; ++j) {
-    if (!(a[j] > 0.0)) bad = true;
-    acc += q[j] * q[j] * log(a[j]);
+  for (int k = threadIdx.x; k < nodes; k += blockDim.x) {
+    const double s = exp(umin + k * kQuadStep);
+    double d = a[m - 1] + s;
+    bool ok = d > 0.0;
+    for (int j = m - 2; j >= 0; --j) {
+      d = a[j] + s - b2[j] / d;
+      ok = ok && (d > 0.0);
+    }
+    if (!ok || !isfinite(d)) bad = 1;
+    acc += s / (1.0 + s) - s / d;
   }
-  gamma[blockIdx.x] = rho0[c] * acc;
-  if (timeout) atomicExch(status, GP_ERR_DEVICE_TIMEOUT);
-  else if (bad) atomicExch(status, GP_ERR_NOT_SPD);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    gamma[blockIdx.x] = rho0[c] * kQuadStep * sum;
+    if (bad) atomicExch(status, GP_ERR_NOT_SPD);
+  }
 }
 
 }  // namespace
@@ -100,11 +100,12 @@ gp_status lanczos_logquad(int count, int c0, int max_iter, const double* alpha,
                           const double* beta, const int* iters, const double* rho0,
                           double* gamma, int* status, cudaStream_t st) {
   if (count == 0) return GP_OK;
-  size_t sm = sizeof(double) * 3 * (size_t)max_iter;
+  const size_t sm = sizeof(double) * 2 * (size_t)max_iter;
   if (sm > 48 * 1024)
     GP_CUDA_TRY(cudaFuncSetAttribute(logquad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sm));
-  logquad_kernel<<<count, 32, sm, st>>>(c0, max_iter, alpha, beta, iters, rho0, gamma, status);
+  logquad_kernel<<<count, kQuadThreads, sm, st>>>(c0, max_iter, alpha, beta, iters, rho0, gamma,
+                                                  status);
   GP_LAUNCH_CHECK();
   return GP_OK;
 }
