@@ -36,8 +36,8 @@
 //               adding up; placing the GEMM1 issuer on the fourth scheduler, next to
 //               the epilogue warps of TMEM lanes 96-127, measured 3-4% faster than
 //               on the second)
-//   warps 3-18  four epilogue warpgroups; warp w reads TMEM lanes 32 (w % 4) .. + 31,
-//               group g = (w - 3) / 4 handles S columns 32 g .. 32 g + 31 of a tile
+//   warps 3-18  epilogue: two teams of eight warps on alternate tiles; warp w reads
+//               TMEM lanes 32 (w % 4) .. + 31 and 64 S columns of its team's tiles
 // Synchronisation uses mbarriers; every wait gives up after a time limit, sets an
 // abort flag and an error code, and the CTA drains its own copies and MMAs (again
 // with a limit) before freeing TMEM and returning.
@@ -355,10 +355,10 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
     mbar_init(smem_u32(&bars->a_free), 1);
     for (int b = 0; b < kSBuf; ++b) {
       mbar_init(smem_u32(&bars->s_full[b]), 1);            // GEMM1 commit
-      mbar_init(smem_u32(&bars->s_free[b]), kEpiWarps);    // each epilogue warp read S
+      mbar_init(smem_u32(&bars->s_free[b]), kEpiWarps / 2);   // each warp of the team read S
     }
     for (int b = 0; b < kPBuf; ++b) {
-      mbar_init(smem_u32(&bars->p_ready[b]), kEpiWarps);   // each epilogue warp wrote P
+      mbar_init(smem_u32(&bars->p_ready[b]), kEpiWarps / 2);  // each warp of the team wrote P
       mbar_init(smem_u32(&bars->p_free[b]), 1);            // GEMM2 commit
     }
     mbar_init(smem_u32(&bars->o_full), 1);
@@ -504,6 +504,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
     // ------------------------------------------------------------ GEMM2 issuer
     const uint32_t id2 = idesc_f16(BM, 2 * tp);   // B = [V_hi; V_lo], N = 2 tp
     const uint32_t id2h = idesc_f16(BM, tp);      // B = V_hi only (split mode)
+    uint32_t t2 = 0;                              // tiles issued (p_free is per tile parity)
     const uint64_t dV0 = sdesc(smem_u32(sV), 128, BN * 16);
     const uint64_t v_step = v_bytes >> 4;
     uint32_t o_par = 0;
@@ -548,7 +549,8 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
             mma_ts(t_o, tpb + 64 + kk * 8, dv + (uint64_t)kk * 16, id2h, 1u);
         }
         mma_commit(smem_u32(&bars->emptyV[st]));
-        mma_commit(smem_u32(&bars->p_free[buf]));
+        mma_commit(smem_u32(&bars->p_free[t2 & 1u]));
+        ++t2;
         if (jj == nt - 1) mma_commit(smem_u32(&bars->o_full));
         sr.next(nsv);
         br.next(npb);
@@ -563,58 +565,87 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
            gtime() - t0 < (unsigned long long)kWaitNs) {
     }
   } else {
-    // ------------------------------------------------------------ epilogue warpgroups
-    // (warps kEpiWarp0 .. kEpiWarp0 + 15)
+    // ------------------------------------------------------------ epilogue warps
+    // (warps kEpiWarp0 .. kEpiWarp0 + 15) in two teams of eight that take alternate
+    // tiles: team 0 the even tiles of the CTA's tile sequence (S buffer 0), team 1 the
+    // odd ones (S buffer 1).  Each warp owns one TMEM lane quarter (its scheduler's)
+    // and 64 columns of its team's tiles, processed as two chunks of 32.  With two
+    // tiles in flight, one team's TMEM loads / stores and barrier waits overlap the
+    // other team's exponentials, which keep the MUFU pipe busy.
+    const int e = warp - kEpiWarp0;
+    const int team = e >> 3;
+    const int half = (e >> 2) & 1;                // columns 64 half .. 64 half + 63
     const int quarter = warp & 3;                 // TMEM lane quarter of this warp
-    const int group = (warp - kEpiWarp0) >> 2;    // S columns 32 g .. 32 g + 31
     const int row = quarter * 32 + lane;          // row within the tile
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    uint32_t of_par = 0;
-    Ring br{0, 0}, pr{0, 0};   // S-buffer ring, P-buffer ring
+    const uint32_t sbuf = (uint32_t)team;         // tile t uses S buffer t % 2
+    uint32_t of_par = 0, gt = 0, mine = 0;        // CTA tile count, this team's count
     for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x) {
       const int rt = u / g.nchunks, ch = u % g.nchunks;
       const int j0 = ch * g.tiles_per_chunk;
       const int j1 = min(g.ntiles, j0 + g.tiles_per_chunk);
       bool ok = true;
-      for (int j = j0; j < j1; ++j) {
-        const uint32_t buf = br.idx;
-        if (!mbar_wait(smem_u32(&bars->s_full[buf]), br.phase, abort, g.err, 31)) {
+      for (int j = j0; j < j1; ++j, ++gt) {
+        if ((gt & 1u) != (uint32_t)team) continue;
+        if (!mbar_wait(smem_u32(&bars->s_full[sbuf]), mine & 1u, abort, g.err, 31)) {
           ok = false;
           break;
         }
+        const uint32_t k = mine++;                // this team's tile index
         tc_fence_after();
-        uint32_t v[32];
-        GP_TMEM_LD32(tmem + buf * 128 + lane_off + group * 32, v);
-        tmem_wait_ld();
-        // S is in registers: release the buffer for the next GEMM1
+        // P buffer of this tile and the GEMM2 that must have completed before it is
+        // rewritten.  p_free[b] completes once per GEMM2 of a tile of parity b, i.e. of
+        // team b's tiles, so every wait below stays within one phase of its barrier
+        // (a parity wait cannot tell phases two apart).
+        //   fast mode (two P buffers): buffer `team`, free after GEMM2 of the team's
+        //     previous tile: phase k - 1 of p_free[team];
+        //   split mode (one P buffer): free after GEMM2 of the previous tile, i.e. of
+        //     the other team's latest tile: phase k - 1 (team 0) or k (team 1) of
+        //     p_free[1 - team].
+        const uint32_t pb = split ? 0u : sbuf;
+        const uint32_t fb = split ? 1u - sbuf : sbuf;
+        const bool wait_p = (split && team == 1) || k >= 1;
+        const uint32_t p_par = (split && team == 1) ? (k & 1u) : ((k - 1u) & 1u);
+#pragma unroll 1
+        for (int c = 0; c < 2 && ok; ++c) {
+          const int col0 = half * 64 + c * 32;
+          uint32_t v[32];
+          GP_TMEM_LD32(tmem + sbuf * 128 + lane_off + col0, v);
+          tmem_wait_ld();
+          if (c == 1) {
+            // both chunks are in registers: release the S buffer for GEMM1
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars->s_free[sbuf]));
+          }
+          if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
+            for (int q = 0; q < 32; ++q) g.dbg[row * BN + col0 + q] = __uint_as_float(v[q]);
+          }
+          uint32_t pk[16], pl[16];
+          if (g.kind == GP_RBF) p_from_s<GP_RBF>(v, pk, pl, split);
+          else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v, pk, pl, split);
+          else p_from_s<GP_MATERN52>(v, pk, pl, split);
+          if (c == 0 && wait_p &&
+              !mbar_wait(smem_u32(&bars->p_free[fb]), p_par, abort, g.err, 33)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          GP_TMEM_ST16(tmem + 256 + pb * 64 + lane_off + col0 / 2, pk);
+          if (split) GP_TMEM_ST16(tmem + 256 + 64 + lane_off + col0 / 2, pl);
+          // tcgen05.st reads its source registers asynchronously: complete it before
+          // the next chunk reuses them
+          tmem_wait_st();
+        }
+        if (!ok) break;
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bars->s_free[buf]));
-        if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
-          for (int q = 0; q < 32; ++q) g.dbg[row * BN + group * 32 + q] = __uint_as_float(v[q]);
-        }
-        uint32_t pk[16], pl[16];
-        if (g.kind == GP_RBF) p_from_s<GP_RBF>(v, pk, pl, split);
-        else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v, pk, pl, split);
-        else p_from_s<GP_MATERN52>(v, pk, pl, split);
-        // the P buffer is free once the GEMM2 that read it two tiles ago has completed
-        if (!mbar_wait(smem_u32(&bars->p_free[pr.idx]), pr.phase ^ 1, abort, g.err, 33)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        GP_TMEM_ST16(tmem + 256 + pr.idx * 64 + lane_off + group * 16, pk);
-        if (split) GP_TMEM_ST16(tmem + 256 + 64 + lane_off + group * 16, pl);
-        tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bars->p_ready[pr.idx]));
-        br.next(kSBuf);
-        pr.next(npb);
+        if (lane == 0) mbar_arrive(smem_u32(&bars->p_ready[pb]));
       }
       if (!ok) break;
-      if (group != 0) continue;
-      // the unit's product is complete: O -> partial output (first group)
+      if (e >= 4) continue;
+      // the unit's product is complete: O -> partial output (warps kEpiWarp0 .. + 3,
+      // one per lane quarter)
       if (!mbar_wait(smem_u32(&bars->o_full), of_par, abort, g.err, 32)) break;
       of_par ^= 1;
       tc_fence_after();
