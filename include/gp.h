@@ -97,17 +97,27 @@ typedef struct {
  * sigma^2 large) that rounding can make K + sigma^2 I indefinite and CG break down
  * (p^T K_hat p <= 0).  The product then has a split mode that carries k(r)/s as FP16
  * hi + lo (22 bits) at about twice the GEMM2 work.
- *   default           fast mode; an eager call (stream not being captured) whose
- *                     CG breaks down reruns CG in split mode.
+ *   default           fast mode.  An eager call (stream not being captured) whose
+ *                     CG breaks down reruns CG in split mode; otherwise, after the
+ *                     evaluation, one product of the CG solutions in each mode gives
+ *                     the first-order change of the MLL had the product been in split
+ *                     mode (d quad = -u^T D u, d logdet ~ (1/l) sum_i (P^-1 z_i)^T D
+ *                     (K^-1 z_i), D = K_split - K_fast); beyond 5e-3 |MLL| (the
+ *                     mixed-precision bound; the estimate overstates large changes
+ *                     about twofold) the evaluation is repeated in split mode.  The
+ *                     estimates are returned in out[GP_OUT_DRIFT_QUAD / _LOGDET].
  *   GP_OPT_SPLIT_P    split mode from the start.
  *   GP_OPT_AUTO_SPLIT choose on the device before CG, from the Gershgorin bound
  *                     lambda_max(K_hat) <= max_i sum_j K_hat_ij (one extra product
  *                     with a vector of ones): split when 2^-11 * bound > 8 sigma^2.
  *                     For graph capture and batched calls, where the host cannot
  *                     rerun CG.  Conservative: some problems it splits would have
- *                     run in fast mode.                                           */
+ *                     run in fast mode.
+ *   GP_OPT_FAST_ONLY  fast mode with neither the rerun nor the check (exactly what
+ *                     a graph-recorded evaluation does).                          */
 #define GP_OPT_SPLIT_P 1
 #define GP_OPT_AUTO_SPLIT 2
+#define GP_OPT_FAST_ONLY 4
 
 /* Which entry point a workspace query is for. */
 typedef enum {
@@ -174,6 +184,9 @@ gp_status gp_mbcg(const gp_problem* prob, const void* L, int64_t ldl, int32_t k,
 #define GP_OUT_LOGDETP 2  /* log det P_hat (determinant lemma)                      */
 #define GP_OUT_STOCH 3    /* (1/l) sum_i gamma_i ~ log det K_hat - log det P_hat    */
 #define GP_OUT_LOGDET 4   /* GP_OUT_LOGDETP + GP_OUT_STOCH                          */
+#define GP_OUT_DRIFT_QUAD 5   /* mixed fast mode: first-order change of y^T u had the */
+#define GP_OUT_DRIFT_LOGDET 6 /* product been in split mode; of log det K_hat (0 if   */
+                              /* not evaluated; see GP_OPT_*)                         */
 #define GP_OUT_HEAD 8
 #define GP_OUT_GRAD(p) (GP_OUT_HEAD)                 /* p entries: dL/dtheta      */
 #define GP_OUT_GK(p) (GP_OUT_HEAD + (p))             /* p: 1/2 u^T dK u - (1/2l) sum_i (K^-1 z_i)^T dK (P^-1 z_i) */

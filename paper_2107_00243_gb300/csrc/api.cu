@@ -321,6 +321,40 @@ inline bool tc_retry_split(const TcBufs& tb, int host_status, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess;
 }
 
+// First-order change of the estimator when the kernel product switches from fast to
+// split mode: with D = (K_split - K_fast) X (X the CG solutions [u, K^-1 z_i]),
+//   d quad   ~ -u^T D_0            (u = K_hat^-1 y),
+//   d logdet ~ (1/l) sum_i (P^-1 z_i)^T D_i
+// (the unbiased trace estimator of tr(K_hat^-1 D), as in the gradient).  Columns are
+// reduced per block in FP64 and combined by the last block: out = {u^T D_0,
+// sum_i (P^-1 z_i)^T D_i}.
+template <class T>
+__global__ void split_drift(int64_t n, int t, const T* __restrict__ X, const T* __restrict__ PinvB,
+                            const T* __restrict__ Wf, const T* __restrict__ Ws,
+                            double* __restrict__ part, unsigned* counter, double* out) {
+  const int nb = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t per = (n + nb - 1) / nb, r0 = blockIdx.x * per, r1 = min(n, r0 + per);
+  for (int c = warp; c < t; c += blockDim.x >> 5) {
+    const T* a = (c == 0 ? X : PinvB) + (int64_t)c * n;
+    double acc = 0.0;
+    for (int64_t i = r0 + lane; i < r1; i += 32)
+      acc += (double)a[i] * ((double)Ws[i + (int64_t)c * n] - (double)Wf[i + (int64_t)c * n]);
+    acc = warp_sum(acc);
+    if (lane == 0) part[(size_t)c * nb + blockIdx.x] = acc;
+  }
+  if (last_block_arrived(counter) && threadIdx.x == 0) {
+    double q = 0.0, tr = 0.0;
+    for (int c = 0; c < t; ++c) {
+      double s = 0.0;
+      for (int b = 0; b < nb; ++b) s += part[(size_t)c * nb + b];
+      if (c == 0) q = s;
+      else tr += s;
+    }
+    out[0] = q;
+    out[1] = tr;
+  }
+}
+
 // ---- gp_mll_and_grad plan -----------------------------------------------------------
 template <class T>
 struct MllPlan {
@@ -406,7 +440,7 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
     GP_TRY(tc_split_setup<T>(pb, op, P.mvm.tc, P.cg.Q, P.cg.R, o, st));
     GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o, P.cg,
                        P.PinvB, pb.n, &host_status, st));
-    if (tc_retry_split(P.mvm.tc, host_status, st)) {
+    if (!(o.flags & GP_OPT_FAST_ONLY) && tc_retry_split(P.mvm.tc, host_status, st)) {
       GP_CUDA_TRY(cudaMemsetAsync(P.cg.status, 0, sizeof(int), st));
       GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o,
                          P.cg, P.PinvB, pb.n, &host_status, st));
@@ -468,6 +502,53 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
     return (gp_status)herr[0];
   }
   if (hstat < 0) return (gp_status)hstat;
+  // Mixed precision in fast mode: estimate the first-order change of the MLL had the
+  // product carried k(r)/s to 22 bits (split mode) instead of 11; beyond the 5e-3
+  // mixed-precision bound, evaluate again in split mode.  Where the change matters,
+  // the first-order estimate overstates it about twofold (measured: n = 1e5 RBF
+  // workload, estimate 3.0e-3 vs. actual 1.5e-3 of |MLL|; a smooth low-noise
+  // problem, 2.9e-2 vs. 1.6e-2), so the bound on the estimate keeps a margin.
+  if (P.mvm.use_tc && !(o.flags & (GP_OPT_SPLIT_P | GP_OPT_AUTO_SPLIT | GP_OPT_FAST_ONLY)) &&
+      nl > 0) {
+    int hsplit = 1;
+    GP_CUDA_TRY(cudaMemcpyAsync(&hsplit, P.mvm.tc.err + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hsplit == 0) {
+      TcMvm op;
+      op.pb = pb;
+      op.tb = P.mvm.tc;
+      GP_TRY(op.apply(P.cg.X, pb.n, t, P.cg.Q, pb.n, nullptr, st));           // fast
+      set_int_kernel<<<1, 1, 0, st>>>(P.mvm.tc.err + 2, 1);
+      GP_LAUNCH_CHECK();
+      GP_TRY(op.apply(P.cg.X, pb.n, t, P.cg.R, pb.n, nullptr, st));           // split
+      set_int_kernel<<<1, 1, 0, st>>>(P.mvm.tc.err + 2, 0);
+      GP_LAUNCH_CHECK();
+      const int nb = (int)std::min<int64_t>(kCgBlocks, cdiv(pb.n, 256));
+      split_drift<T><<<nb, 256, 0, st>>>(pb.n, t, P.cg.X, P.PinvB, P.cg.Q, P.cg.R, P.part,
+                                         P.counter, P.wts);
+      GP_LAUNCH_CHECK();
+      double hd[2] = {0.0, 0.0}, hmll = 0.0;
+      GP_CUDA_TRY(cudaMemcpyAsync(hd, P.wts, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      GP_CUDA_TRY(cudaMemcpyAsync(&hmll, out + GP_OUT_MLL, sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
+      GP_CUDA_TRY(cudaStreamSynchronize(st));
+      const double dd[2] = {-hd[0], hd[1] / nl};   // d quad, d logdet
+      const double dmll = -0.5 * (dd[0] + dd[1]);
+      gp_status r = GP_OK;
+      if (!(fabs(dmll) <= 5e-3 * fabs(hmll))) {
+        gp_opts o2 = o;
+        o2.flags |= GP_OPT_SPLIT_P;
+        r = mll_impl<T>(pb, y, k, nl, eps, piv_override, iters_override, out, iout, o2, ws,
+                        ws_bytes, st, side_index);
+        if (r < 0) return r;
+      }
+      // report the estimates in the output head (GP_OUT_DRIFT_QUAD / _LOGDET)
+      GP_CUDA_TRY(cudaMemcpyAsync(out + GP_OUT_DRIFT_QUAD, dd, 2 * sizeof(double),
+                                  cudaMemcpyHostToDevice, st));
+      GP_CUDA_TRY(cudaStreamSynchronize(st));
+      if (r != GP_OK) return r;
+    }
+  }
   if (hrank < k) return GP_WARN_RANK_DEFICIENT;
   return GP_OK;
 }
@@ -732,7 +813,7 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
     GP_TRY(tc_split_setup<T>(pb, op, mp.tc, cb.Q, cb.R, o, st));
     GP_TRY(cg_solve<T>(pb, op, L, ldl, k, cp.Cinv, B, ldb, t, iters_override, o, cb, PinvB, ldx,
                        &host_status, st));
-    if (tc_retry_split(mp.tc, host_status, st)) {
+    if (!(o.flags & GP_OPT_FAST_ONLY) && tc_retry_split(mp.tc, host_status, st)) {
       GP_CUDA_TRY(cudaMemsetAsync(cb.status, 0, sizeof(int), st));
       GP_TRY(cg_solve<T>(pb, op, L, ldl, k, cp.Cinv, B, ldb, t, iters_override, o, cb, PinvB,
                          ldx, &host_status, st));

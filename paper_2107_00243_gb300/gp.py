@@ -161,7 +161,7 @@ class Problem:
         return ctypes.byref(self._c)
 
 
-OPT_SPLIT_P, OPT_AUTO_SPLIT = 1, 2
+OPT_SPLIT_P, OPT_AUTO_SPLIT, OPT_FAST_ONLY = 1, 2, 4
 
 
 def opts(cg_tol=1e-6, max_iter=200, recompute_every=0, seed=0, pivchol_tol=0.0, check_every=0,
@@ -407,6 +407,7 @@ def unpack(out, iout, p, n_probes, k):
     return {
         "mll": o[OUT_MLL], "quad": o[OUT_QUAD], "logdetP": o[OUT_LOGDETP],
         "stoch": o[OUT_STOCH], "logdet": o[OUT_LOGDET],
+        "drift_quad": o[5], "drift_logdet": o[6],
         "grad": o[h:h + p].copy(), "gK": o[h + p:h + 2 * p].copy(),
         "probeP_p": o[h + 2 * p:h + 3 * p].copy(), "trP_p": o[h + 3 * p:h + 4 * p].copy(),
         "gamma": o[h + 4 * p:h + 4 * p + n_probes].copy(),

@@ -35,7 +35,10 @@ def test_captured_evaluation_matches_eager(precision):
                                  n_probes=8, tol=1e-3, max_iter=400, precision=precision)
     prob = gp.Problem(p.X, p.theta, p.kind, p.ard, precision)
     y = torch.as_tensor(p.y).to(device="cuda", dtype=prob.dtype)
-    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, recompute_every=10, seed=3)
+    # a recorded evaluation neither reruns nor checks (the host reads nothing back), so
+    # the eager side runs with GP_OPT_FAST_ONLY to be the same computation
+    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, recompute_every=10, seed=3,
+                flags=gp.OPT_FAST_ONLY)
     st0, out0, iout0 = _eager(prob, y, p.k, p.n_probes, o)
     assert st0 >= 0
 
@@ -160,3 +163,23 @@ def test_batched_records_graph_with_ill_conditioned_member():
     b.run()
     for r in b.results():
         assert r["status"] == 0 and np.isfinite(r["mll"])
+
+
+def test_fast_mode_accuracy_check_reruns_sensitive_problem():
+    """Member 5 of the small batched family (d = 4, lengthscale near 1, sigma^2 = 0.046):
+    fast mode alone is 1.6% off the FP32 MLL without breaking down; the default eager
+    call detects the drift and returns the split-mode result."""
+    p = workloads.c5_batched(6, seed=0, n_lo=300, n_hi=4000)[5]
+    k, nl = 20, 8
+    res = {}
+    for name, prec, flags in (("fp32", gp.FP32, 0), ("fast", gp.BF16, gp.OPT_FAST_ONLY),
+                              ("default", gp.BF16, 0), ("split", gp.BF16, gp.OPT_SPLIT_P)):
+        prob = gp.Problem(p.X, p.theta, p.kind, p.ard, prec)
+        o = gp.opts(cg_tol=1e-2, max_iter=500, recompute_every=25, seed=11, flags=flags)
+        st, out, iout = _eager(prob, p.y, k, nl, o)
+        assert st == 0
+        res[name] = gp.unpack(out, iout, prob.p, nl, k)["mll"]
+    ref = abs(res["fp32"])
+    assert abs(res["fast"] - res["fp32"]) > 5e-3 * ref          # the hazard is real
+    assert res["default"] == res["split"]
+    assert abs(res["default"] - res["fp32"]) <= 5e-4 * ref
