@@ -387,7 +387,10 @@ void plan_mll(Arena& A, const Prob& pb, int k, int nl, int max_iter, MllPlan<T>&
   P.B = A.take<T>((size_t)pb.n * t);
   P.PinvB = A.take<T>((size_t)pb.n * t);
   P.wts = A.take<double>(t);
-  P.part = A.take<double>(std::max<size_t>(contract_part_elems(pb.n), 4 * kCgBlocks));
+  // block partials of the contraction, dot_into (one per block) and split_drift
+  // (t columns x one per block)
+  const size_t drift = (size_t)t * (size_t)std::min<int64_t>(kCgBlocks, cdiv(pb.n, 256));
+  P.part = A.take<double>(std::max({contract_part_elems(pb.n), (size_t)4 * kCgBlocks, drift}));
   P.counter = A.take<unsigned>(4);
   P.status = A.take<int>(1);
 }

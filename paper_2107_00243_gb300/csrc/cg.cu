@@ -240,27 +240,39 @@ __global__ void reduce_cinv(int k, int t, int ldsp, int nparts, const double* __
   extern __shared__ double sS[];    // k doubles: column c of S
   const int c = blockIdx.y;
   if (!g.active[c]) return;
+  // eight independent chains (fixed order), so eight loads are in flight per thread
+  constexpr int CH = 8;
   for (int m = threadIdx.x; m < k; m += blockDim.x) {
-    double s0 = 0.0, s1 = 0.0;       // two chains over the parts (fixed order)
+    double sc[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) sc[q] = 0.0;
     int b = 0;
-    for (; b + 1 < nparts; b += 2) {
-      s0 += part[((size_t)b * t + c) * k + m];
-      s1 += part[((size_t)(b + 1) * t + c) * k + m];
+    for (; b + CH <= nparts; b += CH) {
+#pragma unroll
+      for (int q = 0; q < CH; ++q) sc[q] += part[((size_t)(b + q) * t + c) * k + m];
     }
-    if (b < nparts) s0 += part[((size_t)b * t + c) * k + m];
-    sS[m] = s0 + s1;
+    for (; b < nparts; ++b) sc[0] += part[((size_t)b * t + c) * k + m];
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < CH; ++q) s += sc[q];
+    sS[m] = s;
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= k) return;
-  double a0 = 0.0, a1 = 0.0;
+  double ac[CH];
+#pragma unroll
+  for (int q = 0; q < CH; ++q) ac[q] = 0.0;
   int m = 0;
-  for (; m + 1 < k; m += 2) {
-    a0 += Cinv[(int64_t)m * k + i] * sS[m];
-    a1 += Cinv[(int64_t)(m + 1) * k + i] * sS[m + 1];
+  for (; m + CH <= k; m += CH) {
+#pragma unroll
+    for (int q = 0; q < CH; ++q) ac[q] += Cinv[(int64_t)(m + q) * k + i] * sS[m + q];
   }
-  if (m < k) a0 += Cinv[(int64_t)m * k + i] * sS[m];
-  g.Sp[(int64_t)i * ldsp + c] = (T)(a0 + a1);
+  for (; m < k; ++m) ac[0] += Cinv[(int64_t)m * k + i] * sS[m];
+  double a = 0.0;
+#pragma unroll
+  for (int q = 0; q < CH; ++q) a += ac[q];
+  g.Sp[(int64_t)i * ldsp + c] = (T)a;
 }
 
 // (3) z = sigma^-2 (r - L Sp) and the partial sums of r^T z for active columns, one

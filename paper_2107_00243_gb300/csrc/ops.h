@@ -119,7 +119,7 @@ struct CgBufs {
   unsigned* counter;         // 1
   int* ctl;                  // 4: device loop control (iteration j, recompute flag and gate)
 };
-constexpr int kCgBlocks = 304;
+constexpr int kCgBlocks = 1216;   // 8 per SM: short per-lane loops in the column reductions
 size_t cg_atb_part_elems(int64_t n, int k, int t);
 size_t cg_part_elems(int64_t n, int t);
 // Matrix-vector product used by CG: W = K_hat V on all t columns; `gate` (device
