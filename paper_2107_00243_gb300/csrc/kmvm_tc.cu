@@ -23,9 +23,11 @@
 //          sigma^2 and CG breaks down (p^T K p <= 0).
 //   split mode (a device flag, read at launch): for smooth, ill-conditioned kernels
 //          (lambda_max(K) / sigma^2 large) even FP16 P can make K + sigma^2 I
-//          indefinite.  Then P is carried as FP16 P_hi + P_lo (22 bits) and GEMM2 adds
-//          P_lo V_hi (N = tp) into O columns [0, tp): 16 MMAs per tile, one 128-column
-//          P buffer instead of two of 64.
+//          indefinite.  Then P is carried as FP16 P_hi + P_lo (22 bits) and GEMM2 also
+//          adds P_lo [V_hi | V_lo] into O (so O_hi + O_lo = (P_hi + P_lo)(V_hi + V_lo)):
+//          16 MMAs per tile, one 128-column P buffer instead of two of 64.
+//   tp = t rounded up to a multiple of 8 (N = 2 tp is then a multiple of 16, as an
+//          M = 128 MMA requires): t = 33 gives N = 80.
 //
 // Roles of a CTA (persistent over (row tile, column chunk) work units):
 //   warp 0      producer: bulk TMA copies (cp.async.bulk) of the pre-tiled A and B tiles
@@ -503,7 +505,6 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   } else if (warp == 2) {
     // ------------------------------------------------------------ GEMM2 issuer
     const uint32_t id2 = idesc_f16(BM, 2 * tp);   // B = [V_hi; V_lo], N = 2 tp
-    const uint32_t id2h = idesc_f16(BM, tp);      // B = V_hi only (split mode)
     uint32_t t2 = 0;                              // tiles issued (p_free is per tile parity)
     const uint64_t dV0 = sdesc(smem_u32(sV), 128, BN * 16);
     const uint64_t v_step = v_bytes >> 4;
@@ -543,10 +544,10 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
 #pragma unroll
         for (int kk = 0; kk < BN / 16; ++kk)
           mma_ts(t_o, tpb + kk * 8, dv + (uint64_t)kk * 16, id2, (kk > 0) ? 1u : acc0);
-        if (split) {   // P_lo V_hi into O columns [0, tp)
+        if (split) {   // P_lo [V_hi | V_lo] into the same O columns
 #pragma unroll
           for (int kk = 0; kk < BN / 16; ++kk)
-            mma_ts(t_o, tpb + 64 + kk * 8, dv + (uint64_t)kk * 16, id2h, 1u);
+            mma_ts(t_o, tpb + 64 + kk * 8, dv + (uint64_t)kk * 16, id2, 1u);
         }
         mma_commit(smem_u32(&bars->emptyV[st]));
         mma_commit(smem_u32(&bars->p_free[t2 & 1u]));
@@ -653,7 +654,9 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
       float* dst = g.part + (size_t)ch * tp * g.npad;
 #pragma unroll 1
       for (int c0 = 0; c0 < tp; c0 += 16) {
-        // tp is a multiple of 16; O = columns [0, tp) (V_hi) + [tp, 2 tp) (V_lo)
+        // O = columns [0, tp) (V_hi) + [tp, 2 tp) (V_lo); when tp is an odd multiple
+        // of 8 the last 16-column load runs past tp (at most to column 2 tp + 7 <= 119
+        // of O, inside the allocation) and the columns >= t are not stored
         uint32_t v[16], w[16];
         GP_TMEM_LD16(t_o + lane_off + c0, v);
         GP_TMEM_LD16(t_o + lane_off + tp + c0, w);
@@ -819,7 +822,7 @@ int sm_count() {
 }
 
 int kx_for(int d) { return 3 * (d + 2) <= 64 ? 64 : 128; }
-int tp_for(int t) { return (t + 15) / 16 * 16; }
+int tp_for(int t) { return (t + 7) / 8 * 8; }
 int ntiles_for(int64_t n) { return (int)cdiv(n, BM); }
 int nchunks_for(int ntiles) {
   int want = (int)cdiv(8LL * 152, ntiles);
