@@ -165,14 +165,16 @@ __global__ void __launch_bounds__(kThreads) cg_init(int64_t n, int t, int max_it
 // L and of the right-hand sides are staged in shared memory with coalesced loads,
 // and each thread keeps a small register tile of the result.
 
-// (1) S_part[b] = L[rows of part b]^T R[rows of part b] for a 64-pivot slice of S.
-//     128 threads; thread (tm, tc) of a 16 x 8 grid owns pivots 4 tm .. 4 tm + 3 and
-//     columns CPT tc .. CPT tc + CPT - 1 (CPT = TC / 8), read from shared memory as
-//     one 16-byte and CPT / 2 8-byte loads per row: 4 CPT FMAs per 1 + CPT / 2 loads.
+// (1) S_part[b] = L[rows of part b]^T R[rows of part b] for a 128-pivot slice of S.
+//     256 threads; thread (tm, tc) of a 32 x 8 grid owns pivots 4 tm .. 4 tm + 3 and
+//     columns CPT tc .. CPT tc + CPT - 1 (CPT = TC / 8).  Rows go through shared memory
+//     in stages of 32; the next stage is loaded into registers while the current one is
+//     multiplied, so the loads of L and R overlap the FMAs.  Each part sums its rows in
+//     order, so the partials do not depend on the slicing.
 constexpr int kLtrRows = 32;
-constexpr int kLtrM = 64;
-constexpr int kLtrParts = 152;    // row parts; x (k / 64) slices ~ 4 CTAs per SM
-constexpr int kLtrThreads = 128;
+constexpr int kLtrM = 128;
+constexpr int kLtrParts = 152;    // row parts; x (k / 128) slices
+constexpr int kLtrThreads = 256;
 template <class T, int TC>
 __global__ void __launch_bounds__(kLtrThreads) ltr_partial(int64_t n, int t,
                                                           const T* __restrict__ L, int64_t ldl,
@@ -181,9 +183,11 @@ __global__ void __launch_bounds__(kLtrThreads) ltr_partial(int64_t n, int t,
   constexpr int CPT = TC / 8;
   constexpr int LP = kLtrM + 16 / (int)sizeof(T);   // row pitch: 16-byte aligned rows
   constexpr int RP = TC + 2;
+  constexpr int NL = kLtrRows * kLtrM / kLtrThreads;                   // 16 L values
+  constexpr int NR = (kLtrRows * TC + kLtrThreads - 1) / kLtrThreads;  // <= CPT R values
   __shared__ __align__(16) T sL[kLtrRows][LP];
   __shared__ __align__(16) T sR[kLtrRows][RP];
-  const int tm = threadIdx.x & 15, tcol = threadIdx.x >> 4;
+  const int tm = threadIdx.x & 31, tcol = threadIdx.x >> 5;
   const int m0 = blockIdx.x * kLtrM;
   const int64_t per = (n + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = blockIdx.y * per, r1 = min(n, r0 + per);
@@ -192,18 +196,39 @@ __global__ void __launch_bounds__(kLtrThreads) ltr_partial(int64_t n, int t,
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int c = 0; c < CPT; ++c) acc[a][c] = T(0);
-  for (int64_t rb = r0; rb < r1; rb += kLtrRows) {
+  // element e of a stage: row e % 32 (consecutive threads on consecutive rows: coalesced),
+  // pivot / column e / 32
+  T pl[NL], pr[NR];
+  auto fetch = [&](int64_t rb) {
     const int rn = (int)min((int64_t)kLtrRows, r1 - rb);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kLtrRows * kLtrM; e += kLtrThreads) {
-      const int rr = e % kLtrRows, mm = e / kLtrRows;     // rows fastest: coalesced
-      sL[rr][mm] = (rr < rn && m0 + mm < k) ? L[rb + rr + (int64_t)(m0 + mm) * ldl] : T(0);
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + q * kLtrThreads;
+      const int rr = e % kLtrRows, mm = e / kLtrRows;
+      pl[q] = (rr < rn && m0 + mm < k) ? L[rb + rr + (int64_t)(m0 + mm) * ldl] : T(0);
     }
-    for (int e = threadIdx.x; e < kLtrRows * TC; e += kLtrThreads) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const int e = threadIdx.x + q * kLtrThreads;
       const int rr = e % kLtrRows, c = e / kLtrRows;
-      sR[rr][c] = (rr < rn && c < t) ? g.R[rb + rr + (int64_t)c * n] : T(0);
+      pr[q] = (e < kLtrRows * TC && rr < rn && c < t) ? g.R[rb + rr + (int64_t)c * n] : T(0);
+    }
+  };
+  if (r0 < r1) fetch(r0);
+  for (int64_t rb = r0; rb < r1; rb += kLtrRows) {
+    __syncthreads();                 // the previous stage has been read
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + q * kLtrThreads;
+      sL[e % kLtrRows][e / kLtrRows] = pl[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const int e = threadIdx.x + q * kLtrThreads;
+      if (e < kLtrRows * TC) sR[e % kLtrRows][e / kLtrRows] = pr[q];
     }
     __syncthreads();
+    if (rb + kLtrRows < r1) fetch(rb + kLtrRows);   // in flight during the FMAs below
 #pragma unroll 4
     for (int rr = 0; rr < kLtrRows; ++rr) {
       T lv[4], rv[CPT];
@@ -277,7 +302,9 @@ __global__ void reduce_cinv(int k, int t, int ldsp, int nparts, const double* __
 
 // (3) z = sigma^-2 (r - L Sp) and the partial sums of r^T z for active columns, one
 //     128-row tile per block.  Thread (tr, tc) of a 32 x 8 grid owns rows
-//     4 tr .. 4 tr + 3 and columns CPT tc .. CPT tc + CPT - 1.
+//     4 tr .. 4 tr + 3 and columns CPT tc .. CPT tc + CPT - 1.  Pivots go through shared
+//     memory in chunks of 32; the next chunk of L and Sp is loaded into registers while
+//     the current one is multiplied.
 constexpr int kPrRows = 128;
 constexpr int kPrM = 32;
 template <class T, int TC>
@@ -287,6 +314,8 @@ __global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, int c0
                                                        int D, Dev<T> g) {
   if (*g.n_active == 0) return;
   constexpr int CPT = TC / 8;
+  constexpr int NL = kPrM * kPrRows / kThreads;                  // 16 L values
+  constexpr int NS = (kPrM * TC + kThreads - 1) / kThreads;      // <= CPT Sp values
   __shared__ __align__(16) T sL[kPrM][kPrRows];
   __shared__ T sSp[kPrM][TC];
   __shared__ double swarp[kThreads / 32][TC];
@@ -300,19 +329,41 @@ __global__ void __launch_bounds__(kThreads) precond_rho(int64_t n, int t, int c0
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int c = 0; c < CPT; ++c) acc[a][c] = T(0);
-  for (int m0 = 0; m0 < k; m0 += kPrM) {
+  // L element e of a chunk: row e % 128 (coalesced), pivot e / 128; Sp element e:
+  // pivot e / TC, column e % TC
+  T pl[NL], ps[NS];
+  auto fetch = [&](int m0) {
     const int mn = min(kPrM, k - m0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kPrM * kPrRows; e += kThreads) {
-      const int rr = e % kPrRows, mm = e / kPrRows;      // rows fastest: coalesced
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + q * kThreads;
+      const int rr = e % kPrRows, mm = e / kPrRows;
       const int64_t a = a0 + rr;
-      sL[mm][rr] = (mm < mn && a < n) ? L[a + (int64_t)(m0 + mm) * ldl] : T(0);
+      pl[q] = (mm < mn && a < n) ? L[a + (int64_t)(m0 + mm) * ldl] : T(0);
     }
-    for (int e = threadIdx.x; e < kPrM * TC; e += kThreads) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const int e = threadIdx.x + q * kThreads;
       const int mm = e / TC, c = e % TC;
-      sSp[mm][c] = (mm < mn && c < tc) ? g.Sp[(int64_t)(m0 + mm) * t + c0 + c] : T(0);
+      ps[q] = (e < kPrM * TC && mm < mn && c < tc) ? g.Sp[(int64_t)(m0 + mm) * t + c0 + c]
+                                                   : T(0);
+    }
+  };
+  fetch(0);
+  for (int m0 = 0; m0 < k; m0 += kPrM) {
+    __syncthreads();                 // the previous chunk has been read
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + q * kThreads;
+      sL[e / kPrRows][e % kPrRows] = pl[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const int e = threadIdx.x + q * kThreads;
+      if (e < kPrM * TC) sSp[e / TC][e % TC] = ps[q];
     }
     __syncthreads();
+    if (m0 + kPrM < k) fetch(m0 + kPrM);   // in flight during the FMAs below
 #pragma unroll 8
     for (int mm = 0; mm < kPrM; ++mm) {
       T lv[4], sv[CPT];
@@ -615,12 +666,13 @@ cudaStream_t capture_body_stream() {
   return bs.s;
 }
 
-int pick_tc16(int t) { return t <= 16 ? 16 : t <= 32 ? 32 : t <= 48 ? 48 : 64; }
+int pick_tc16(int t) { return t <= 16 ? 16 : t <= 32 ? 32 : t <= 40 ? 40 : t <= 48 ? 48 : 64; }
 
 #define GP_TC_DISPATCH(TCv, ...)                        \
   switch (TCv) {                                        \
     case 16: { constexpr int TC = 16; __VA_ARGS__; } break; \
     case 32: { constexpr int TC = 32; __VA_ARGS__; } break; \
+    case 40: { constexpr int TC = 40; __VA_ARGS__; } break; \
     case 48: { constexpr int TC = 48; __VA_ARGS__; } break; \
     default: { constexpr int TC = 64; __VA_ARGS__; } break; \
   }
