@@ -69,6 +69,23 @@ def _traffic_from_profiles(kernel_tag):
     return None
 
 
+def _unit_peak(key):
+    """A measured unit throughput from profiles/unit_peaks_gb300.txt (key, value), or
+    None when the file or the key is missing."""
+    path = os.path.join(ROOT, "profiles", "unit_peaks_gb300.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 2 and parts[0] == key:
+                try:
+                    return float(parts[1])
+                except ValueError:
+                    return None
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
 
@@ -217,6 +234,40 @@ def run_reference(args, rank, ws, dist):
     _barrier(dist)
 
 
+def run_peaks():
+    """Throughput peaks the driver's copy / BF16 GEMM measurements do not cover: FP32 FMA,
+    MUFU ex2 (FP32 and FP16x2), FP64 FMA (the library's microbenchmarks), and TF32 GEMM
+    (cuBLAS through torch.matmul, 8192^3, best of 5)."""
+    import torch
+    from paper_2107_00243_gb300 import build, gp
+    build.build()
+    gp.load()
+    res = gp.measure_peaks()
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        torch.matmul(a, b)
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    res["tf32_gemm_flops"] = 2.0 * n ** 3 / best
+    dev = torch.cuda.get_device_properties(0)
+    res["device"] = dev.name
+    res["sms"] = dev.multi_processor_count
+    print(json.dumps({k: (float(f"{v:.4g}") if isinstance(v, float) else v)
+                      for k, v in res.items()}))
+
+
 def run_case(args):
     """Time one building block on a smaller instance of the workload (same d, kernel,
     hyperparameters; n points drawn the same way).  Used for profiling captures."""
@@ -335,7 +386,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=1,
                     help="timed steps of the plain FP32 form when --precision is mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg", "batched"],
+    ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg", "batched", "peaks"],
                     default="estimator",
                     help="kmvm / mbcg: time only the kernel product or a short CG call on a "
                          "smaller instance of the workload (for profiling)")
@@ -344,6 +395,9 @@ def main():
     args = ap.parse_args()
     if args.case == "batched":
         run_batched(args)
+        return
+    if args.case == "peaks":
+        run_peaks()
         return
     if args.case != "estimator":
         run_case(args)
@@ -482,6 +536,14 @@ def main():
             "traffic": _traffic_from_profiles(kernel_tag), "kernel": kernel_tag,
             "peak_source": peak_note, "algorithmic_flops_per_product": flops_per,
             "products_timed": mvm_n, "avg_product_ms": avg_mvm_s * 1e3}
+    # the product's other roofline: one exponential per kernel entry (n^2 per product)
+    # against the measured MUFU ex2 rate
+    ex2_peak = _unit_peak("ex2_f32_per_s")
+    if avg_mvm_s and ex2_peak:
+        ex2_rate = float(p.n) ** 2 / avg_mvm_s
+        roof["exp"] = {"achieved": ex2_rate, "peak": ex2_peak, "unit": "exp/s",
+                       "frac": ex2_rate / ex2_peak,
+                       "peak_source": "ex2.approx.f32, measured (profiles/unit_peaks_gb300.txt)"}
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:

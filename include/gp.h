@@ -318,6 +318,17 @@ int64_t gp_launch_count(void);
 void gp_mvm_timing(int32_t enable);
 gp_status gp_mvm_timing_read(double* total_ms, int64_t* products);
 
+/* Throughput microbenchmarks of the arithmetic units the path uses (roofline
+ * denominators beside the measured copy bandwidth and BF16 GEMM rate):
+ *   out[0] FP32 FMA FLOP/s, out[1] ex2.approx.f32 results/s (MUFU),
+ *   out[2] ex2.approx.f16x2 results/s (two per instruction), out[3] FP64 FMA FLOP/s.
+ * Each kernel runs independent dependency chains, 8 CTAs of 256 threads per SM,
+ * timed with CUDA events on `stream` (best of three after a warm-up launch).
+ * scratch: device, at least gp_peaks_scratch_elems() floats, overwritten.  out: host,
+ * 4 doubles.  Synchronous: returns after the timings (about 0.2 s).               */
+size_t gp_peaks_scratch_elems(void);
+gp_status gp_measure_peaks(float* scratch, double* out, gp_stream_t stream);
+
 /* Rademacher signs of the probe generator, for inspection:
  * out[c * rows + r] = +-1 for stream 1 (eps1) or 2 (eps2).  Asynchronous.         */
 gp_status gp_rademacher(uint64_t seed, int32_t stream_id, int64_t rows, int32_t cols,

@@ -86,6 +86,8 @@ def load():
         "gp_tc_config": (i32, [P, i32, vp]),
         "gp_mll_and_grad_batched": (i32, [i32, P, vp, i32, i32, vp, vp, O, vp, sz, vp]),
         "gp_launch_count": (i64, []),
+        "gp_peaks_scratch_elems": (sz, []),
+        "gp_measure_peaks": (i32, [vp, ctypes.POINTER(ctypes.c_double), vp]),
         "gp_mvm_timing": (None, [i32]),
         "gp_mvm_timing_read": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
     }
@@ -432,6 +434,17 @@ def launch_count():
 
 def mvm_timing(enable):
     load().gp_mvm_timing(1 if enable else 0)
+
+
+def measure_peaks():
+    """Measured throughputs of the units the path uses (gp_measure_peaks): FP32 FMA
+    FLOP/s, ex2.approx.f32 results/s, ex2.approx.f16x2 results/s, FP64 FMA FLOP/s."""
+    lib = load()
+    scratch = torch.empty(int(lib.gp_peaks_scratch_elems()), dtype=torch.float32, device="cuda")
+    out = (ctypes.c_double * 4)()
+    _check("gp_measure_peaks", lib.gp_measure_peaks(_ptr(scratch), out, _stream()))
+    return {"fp32_fma_flops": out[0], "ex2_f32_per_s": out[1], "ex2_f16x2_per_s": out[2],
+            "fp64_fma_flops": out[3]}
 
 
 def mvm_timing_read():
