@@ -2,7 +2,7 @@
 
 Every translation unit under ``csrc/`` is compiled by nvcc in parallel and linked
 into one shared library with the CUDA runtime linked statically, so the library
-depends on nothing but the driver at run time.  The build is skipped when the
+depends on nothing but the CUDA driver at run time.  The build is skipped when the
 library is newer than every source and header.
 """
 import concurrent.futures as cf
