@@ -235,7 +235,7 @@ def run_reference(args, rank, ws, dist):
 
 
 def run_peaks():
-    """Throughput peaks the driver's copy / BF16 GEMM measurements do not cover: FP32 FMA,
+    """Throughput peaks the HBM-copy and BF16-GEMM measurements do not cover: FP32 FMA,
     MUFU ex2 (FP32 and FP16x2), FP64 FMA (the library's microbenchmarks), and TF32 GEMM
     (cuBLAS through torch.matmul, 8192^3, best of 5)."""
     import torch

@@ -1,5 +1,5 @@
 // Throughput microbenchmarks of the arithmetic units on the estimator's path, for the
-// roofline denominators that the driver's copy / cuBLAS measurements do not give:
+// roofline denominators that the HBM-copy and BF16-GEMM measurements do not give:
 //   FP32 FMA (the FP32 kernel product and the CG vector kernels),
 //   ex2.approx.f32 on the MUFU pipe (one per kernel entry in the tensor-core product),
 //   ex2.approx.f16x2 (two results per instruction),
