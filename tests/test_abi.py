@@ -61,6 +61,8 @@ def test_invalid_arguments_rejected_on_host(lib):
                                ctypes.byref(o), None, 0, None) == -1          # k > n
     assert lib.gp_pivchol(None, 2, 0.0, None, None, 10, None, None, None, 0, None) == -1
     assert lib.gp_rademacher(0, 3, 10, 1, 8, None) == -1
+    assert lib.gp_measure_peaks(None, None, None) == -1   # rejected before any launch
+    assert lib.gp_peaks_scratch_elems() >= 8 * 256
 
 
 def test_batched_workspace_size_is_sum_of_aligned_slices():
