@@ -24,6 +24,12 @@ class MarginalLogLikelihood(torch.autograd.Function):
     def forward(ctx, theta, problem, y, k, n_probes, opts, workspace=None):
         problem.set_theta(theta.detach().to(torch.float64))
         st, out, iout = gp.gp_mll_and_grad(problem, y, k, n_probes, opts, workspace=workspace)
+        dev_status = int(iout[gp.IOUT_STATUS].item())
+        if st < 0 or dev_status < 0:
+            code = st if st < 0 else dev_status
+            raise RuntimeError(f"gp_mll_and_grad failed: {gp.status_string(code)}")
+        if not bool(torch.isfinite(out[gp.OUT_MLL]).item()):
+            raise RuntimeError("gp_mll_and_grad returned a non-finite MLL")
         p = problem.p
         grad = out[gp.OUT_HEAD:gp.OUT_HEAD + p].to(theta.device, theta.dtype)
         ctx.save_for_backward(grad)
@@ -54,9 +60,7 @@ def adam_fit(problem, y, theta0, k, n_probes, opts, steps=20, lr=0.05, betas=(0.
     ws = gp.Workspace()
     history = []
     for step in range(steps):
-        o = gp.opts(cg_tol=opts.cg_tol, max_iter=opts.max_iter,
-                    recompute_every=opts.recompute_every, seed=seed0 + step,
-                    pivchol_tol=opts.pivchol_tol, check_every=opts.check_every)
+        o = gp.opts_with(opts, seed=seed0 + step)   # every other option as the caller set it
         x = phi.clone().requires_grad_(True)
         val = mll(torch.exp(x), problem, y, k, n_probes, o, ws)
         (-val).backward()

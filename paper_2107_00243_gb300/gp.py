@@ -28,6 +28,7 @@ STATUS = {0: "GP_OK", 1: "GP_WARN_NOT_CONVERGED", 2: "GP_WARN_RANK_DEFICIENT",
           -4: "GP_ERR_WORKSPACE", -5: "GP_ERR_DEVICE_TIMEOUT", -6: "GP_ERR_NUMERIC"}
 
 OUT_MLL, OUT_QUAD, OUT_LOGDETP, OUT_STOCH, OUT_LOGDET, OUT_HEAD = 0, 1, 2, 3, 4, 8
+IOUT_STATUS, IOUT_RANK, IOUT_ITERS = 0, 1, 2
 
 
 class GPError(RuntimeError):
@@ -170,6 +171,21 @@ def opts(cg_tol=1e-6, max_iter=200, recompute_every=0, seed=0, pivchol_tol=0.0, 
          flags=0):
     return _Opts(float(cg_tol), int(max_iter), int(recompute_every), int(seed),
                  float(pivchol_tol), int(check_every), int(flags))
+
+
+def status_string(code):
+    """Name of a gp_status code."""
+    return load().gp_status_string(int(code)).decode()
+
+
+def opts_with(o, **changes):
+    """A copy of the options struct `o` with the named fields replaced."""
+    fields = {name: getattr(o, name) for name, _ in _Opts._fields_}
+    for name, value in changes.items():
+        if name not in fields:
+            raise KeyError(f"gp_opts has no field {name!r}")
+        fields[name] = value
+    return opts(**fields)
 
 
 def gp_workspace_size(fn, n, d, k, t, precision, max_iter=1):

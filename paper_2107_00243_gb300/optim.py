@@ -103,7 +103,8 @@ def lbfgs_minimize(fun, x0, m=10, max_iter=100, gtol=1e-5, ftol=1e-10, c1=1e-4, 
                    max_ls=20, validation=None, patience=3, callback=None):
     """Minimise fun over x (1-D float64 array).  fun(x) -> (f, g).
 
-    Stops when max|g| <= gtol, when the relative decrease of f in an iteration is below
+    Returns at once with reason "eval_failed" when f or g is not finite at x0.
+    Otherwise stops when max|g| <= gtol, when the relative decrease of f in an iteration is below
     ftol (ftol = 0: never), after max_iter iterations, when a line search fails, or (with validation(x)
     -> loss) after `patience` iterations without a new best validation loss; then the
     best-validated iterate is returned.  Returns a dict with x, f, g, nit, nfev, reason
@@ -122,6 +123,10 @@ def lbfgs_minimize(fun, x0, m=10, max_iter=100, gtol=1e-5, ftol=1e-10, c1=1e-4, 
         hist["val"].append(best_val)
     reason = "max_iter"
     nit = 0
+    if not (math.isfinite(f) and np.all(np.isfinite(g))):
+        # the objective cannot be evaluated at the start: nothing to optimise
+        return {"x": x, "f": f, "g": g, "nit": 0, "nfev": nfev, "reason": "eval_failed",
+                "history": hist}
     for nit in range(1, max_iter + 1):
         if np.max(np.abs(g)) <= gtol:
             reason = "gtol"

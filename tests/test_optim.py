@@ -146,3 +146,31 @@ def test_lbfgs_fit_plumbing_with_exact_objective(monkeypatch):
     assert np.allclose(theta, np.exp(direct["x"]), rtol=1e-10)
     assert np.allclose(prob.theta, theta)
     assert res["f"] == pytest.approx(direct["f"], rel=1e-14)
+
+
+def test_failed_start_is_not_reported_converged():
+    """An objective that cannot be evaluated at x0 (inf, zero gradient) ends the run
+    with reason 'eval_failed', not 'gtol'."""
+    res = optim.lbfgs_minimize(lambda x: (math.inf, np.zeros_like(x)), np.zeros(3))
+    assert res["reason"] == "eval_failed"
+    assert res["nit"] == 0 and res["nfev"] == 1
+
+
+def test_lbfgs_fit_failed_evaluation_at_start(monkeypatch):
+    """lbfgs_fit on an estimator that reports a device-side error at theta0."""
+    torch = pytest.importorskip("torch")
+    from paper_2107_00243_gb300 import gp
+
+    class FakeProblem:
+        p = 3
+
+        def set_theta(self, th):
+            self.theta = np.array(th)
+
+    monkeypatch.setattr(gp, "gp_mll_and_grad", lambda *a, **kw: (0, None, None))
+    monkeypatch.setattr(gp, "unpack", lambda *a: {"mll": 1.0, "grad": np.ones(3),
+                                                  "status": -3})
+    monkeypatch.setattr(gp, "Workspace", lambda: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    _, res = optim.lbfgs_fit(FakeProblem(), None, np.ones(3), 0, 0, None)
+    assert res["reason"] == "eval_failed"
