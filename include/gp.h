@@ -118,6 +118,10 @@ typedef struct {
 #define GP_OPT_SPLIT_P 1
 #define GP_OPT_AUTO_SPLIT 2
 #define GP_OPT_FAST_ONLY 4
+/* GP_OPT_SIMT_GRAD  in GP_BF16 precision, run the gradient contraction of Alg. 2 on
+ *                   CUDA cores in FP32 instead of on the tensor cores (the default
+ *                   for d <= 31 and t <= 64; see gp_mll_and_grad).                */
+#define GP_OPT_SIMT_GRAD 8
 
 /* Which entry point a workspace query is for. */
 typedef enum {
@@ -267,7 +271,7 @@ gp_status gp_autotune(const gp_problem* prob, const void* V, int64_t ldv, int32_
  * {chunks, B ring, V ring, 1 if from the autotuner else 0}.  Host only.           */
 gp_status gp_tc_config(const gp_problem* prob, int32_t t, int32_t* config);
 
-/* Human-readable name of a status code (static storage). *//* Human-readable name of a status code (static storage). */
+/* Human-readable name of a status code (static storage). */
 const char* gp_status_string(int32_t status);
 
 /* Detail of the last host-side validation failure on this thread (static storage). */
@@ -317,6 +321,11 @@ gp_status gp_tc_exponent_tile(const gp_problem* prob, const void* V, int64_t ldv
 int64_t gp_launch_count(void);
 void gp_mvm_timing(int32_t enable);
 gp_status gp_mvm_timing_read(double* total_ms, int64_t* products);
+/* The same timing for a phase of gp_mll_and_grad: phase 0 = the kernel-matrix
+ * products (as gp_mvm_timing_read), phase 1 = the gradient contraction of Alg. 2
+ * (one bracket per evaluation).  Returns (and resets) the summed duration in ms and
+ * the number of brackets.                                                         */
+gp_status gp_phase_timing_read(int32_t phase, double* total_ms, int64_t* count);
 
 /* Throughput microbenchmarks of the arithmetic units the path uses (roofline
  * denominators beside the measured copy bandwidth and BF16 GEMM rate):

@@ -363,6 +363,8 @@ struct MllPlan {
   CorePlan core;
   CgBufs<T> cg;
   PrecBufs prec;
+  TcGradBufs tg;     // tensor-core gradient contraction (use_tg)
+  bool use_tg;
   T* L;
   int* pivots;
   int* rank;
@@ -381,6 +383,15 @@ void plan_mll(Arena& A, const Prob& pb, int k, int nl, int max_iter, MllPlan<T>&
   plan_core(A, pb, k, P.core);
   plan_cg<T>(A, pb, k, t, max_iter, P.cg);
   plan_prec(A, pb, k, nl, P.prec);
+  P.use_tg = P.mvm.use_tc && tc_grad_supported(pb, t);
+  P.tg = TcGradBufs{};
+  if (P.use_tg) {
+    P.tg.pack = A.take<char>(tc_grad_bytes(pb.n, pb.d, t));
+    P.tg.part = A.take<double>(tc_grad_part_elems());
+    P.tg.cmax = A.take<int>(128);
+    P.tg.mscale = A.take<float>(128);
+    P.tg.inv2E = A.take<double>(1);
+  }
   P.L = A.take<T>((size_t)pb.n * std::max(k, 1));
   P.pivots = A.take<int>(std::max(k, 1));
   P.rank = A.take<int>(1);
@@ -475,8 +486,20 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   GP_LAUNCH_CHECK();
   fill_weights<<<(unsigned)cdiv(t, 128), 128, 0, st>>>(t, P.wts);
   GP_LAUNCH_CHECK();
-  GP_TRY(contract_simt<T>(pb, Xs, P.cg.X, pb.n, P.PinvB, pb.n, P.wts, t, P.part, P.counter,
-                          out + GP_OUT_GK(pb.p), st));
+  const bool timed = mvm_timing_enabled();
+  if (timed) mvm_timing_begin(st, 1);
+  if (P.use_tg && !(o.flags & GP_OPT_SIMT_GRAD)) {
+    GP_TRY(tc_grad_prepare(pb, Xs, P.tg, t, st));
+    GP_TRY(contract_tc(pb, Xs, P.mvm.tc, P.tg, reinterpret_cast<const float*>(P.cg.X), pb.n,
+                       reinterpret_cast<const float*>(P.PinvB), pb.n, P.wts, t,
+                       out + GP_OUT_GK(pb.p), st));
+    GP_TRY(contract_noise<T>(pb, P.cg.X, pb.n, P.PinvB, pb.n, P.wts, t, P.part, P.counter,
+                             out + GP_OUT_GK(pb.p) + pb.D + 1, st));
+  } else {
+    GP_TRY(contract_simt<T>(pb, Xs, P.cg.X, pb.n, P.PinvB, pb.n, P.wts, t, P.part, P.counter,
+                            out + GP_OUT_GK(pb.p), st));
+  }
+  if (timed) mvm_timing_end(st, 1);
   // S10: preconditioner terms with W = P^-1 z_i (columns 1..l of PinvB)
   GP_TRY(precond_terms<T>(pb, Xs, P.L, pb.n, k, P.pivots, P.rank, P.PinvB + pb.n, pb.n, nl,
                           P.core.Cinv, P.prec, out + GP_OUT_TRP(pb.p), out + GP_OUT_PROBEP(pb.p),
@@ -1140,8 +1163,8 @@ std::atomic<long long> g_launches{0};
 std::atomic<int> g_timing{0};
 std::mutex g_tmu;
 std::vector<cudaEvent_t> g_free_events;
-std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_pairs;
-cudaEvent_t g_open = nullptr;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_pairs[2];   // per phase
+cudaEvent_t g_open[2] = {nullptr, nullptr};
 cudaEvent_t take_event() {
   if (!g_free_events.empty()) {
     cudaEvent_t e = g_free_events.back();
@@ -1156,19 +1179,37 @@ cudaEvent_t take_event() {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 bool mvm_timing_enabled() { return g_timing.load() != 0; }
-void mvm_timing_begin(cudaStream_t st) {
+void mvm_timing_begin(cudaStream_t st, int phase) {
   std::lock_guard<std::mutex> lk(g_tmu);
-  g_open = take_event();
-  if (g_open) cudaEventRecord(g_open, st);
+  g_open[phase] = take_event();
+  if (g_open[phase]) cudaEventRecord(g_open[phase], st);
 }
-void mvm_timing_end(cudaStream_t st) {
+void mvm_timing_end(cudaStream_t st, int phase) {
   std::lock_guard<std::mutex> lk(g_tmu);
-  if (!g_open) return;
+  if (!g_open[phase]) return;
   cudaEvent_t e = take_event();
   if (!e) return;
   cudaEventRecord(e, st);
-  g_pairs.emplace_back(g_open, e);
-  g_open = nullptr;
+  g_pairs[phase].emplace_back(g_open[phase], e);
+  g_open[phase] = nullptr;
+}
+gp_status phase_timing_read(int phase, double* total_ms, int64_t* count) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  double tot = 0.0;
+  int64_t cnt = 0;
+  for (auto& pr : g_pairs[phase]) {
+    GP_CUDA_TRY(cudaEventSynchronize(pr.second));
+    float ms = 0.f;
+    GP_CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    tot += ms;
+    ++cnt;
+    g_free_events.push_back(pr.first);
+    g_free_events.push_back(pr.second);
+  }
+  g_pairs[phase].clear();
+  if (total_ms) *total_ms = tot;
+  if (count) *count = cnt;
+  return GP_OK;
 }
 }  // namespace gp
 
@@ -1177,22 +1218,12 @@ extern "C" int64_t gp_launch_count(void) { return (int64_t)gp::g_launches.load()
 extern "C" void gp_mvm_timing(int32_t enable) { gp::g_timing.store(enable ? 1 : 0); }
 
 extern "C" gp_status gp_mvm_timing_read(double* total_ms, int64_t* products) {
-  std::lock_guard<std::mutex> lk(gp::g_tmu);
-  double tot = 0.0;
-  int64_t cnt = 0;
-  for (auto& pr : gp::g_pairs) {
-    GP_CUDA_TRY(cudaEventSynchronize(pr.second));
-    float ms = 0.f;
-    GP_CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
-    tot += ms;
-    ++cnt;
-    gp::g_free_events.push_back(pr.first);
-    gp::g_free_events.push_back(pr.second);
-  }
-  gp::g_pairs.clear();
-  if (total_ms) *total_ms = tot;
-  if (products) *products = cnt;
-  return GP_OK;
+  return gp::phase_timing_read(0, total_ms, products);
+}
+
+extern "C" gp_status gp_phase_timing_read(int32_t phase, double* total_ms, int64_t* count) {
+  GP_REQUIRE(phase == 0 || phase == 1, "phase must be 0 or 1");
+  return gp::phase_timing_read(phase, total_ms, count);
 }
 
 extern "C" gp_status gp_tc_exponent_tile(const gp_problem* prob, const void* V, int64_t ldv,

@@ -536,6 +536,25 @@ gp_status contract_simt(const Prob& pb, const void* Xs_, const void* A_, int64_t
   return GP_OK;
 }
 
+template <class T>
+gp_status contract_noise(const Prob& pb, const void* A_, int64_t lda, const void* B_, int64_t ldb,
+                         const double* wts, int t, double* part, unsigned* counter, double* gout,
+                         cudaStream_t st) {
+  const T* A = static_cast<const T*>(A_);
+  const T* B = static_cast<const T*>(B_);
+  int blocks = (int)std::min<int64_t>(cdiv(pb.n, 256), 256);
+  diag_contract_kernel<T><<<blocks, 256, 0, st>>>(pb.n, A, lda, B, ldb, wts, t, part, counter,
+                                                  gout);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+template gp_status contract_noise<float>(const Prob&, const void*, int64_t, const void*, int64_t,
+                                         const double*, int, double*, unsigned*, double*,
+                                         cudaStream_t);
+template gp_status contract_noise<double>(const Prob&, const void*, int64_t, const void*, int64_t,
+                                          const double*, int, double*, unsigned*, double*,
+                                          cudaStream_t);
+
 template gp_status prep_inputs<float>(const Prob&, const PrepBufs&, cudaStream_t);
 template gp_status prep_inputs<double>(const Prob&, const PrepBufs&, cudaStream_t);
 template gp_status kmvm_simt<float>(const Prob&, const void*, const void*, int64_t, int, void*,

@@ -64,6 +64,32 @@ void tc_config(const Prob& pb, int t, int* out4);
 gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
                         float* W, int64_t ldw, const int* gate, float* dbg, cudaStream_t st);
 
+// ---- tensor-core gradient contraction (grad_tc.cu) ---------------------------------
+// The contraction of contract_simt (lengthscale and output-scale entries) for the
+// mixed precision on tcgen05 tensor cores; the noise entry comes from contract_noise.
+struct TcGradBufs {
+  void* pack;        // tc_grad_bytes(n, d, t): M operand tiles A', B' and coordinate tiles
+  double* part;      // tc_grad_part_elems(): per-CTA partial sums
+  int* cmax;         // 2 x 64: column maxima of |A| and |B|
+  float* mscale;     // 2 x 64: power-of-two column scales of A' and B'
+  double* inv2E;     // 1
+};
+bool tc_grad_supported(const Prob& pb, int t);
+size_t tc_grad_bytes(int64_t n, int d, int t);
+size_t tc_grad_part_elems();
+// coordinate tiles of the scaled inputs (once per evaluation)
+gp_status tc_grad_prepare(const Prob& pb, const void* Xs, const TcGradBufs& gb, int t,
+                          cudaStream_t st);
+// gout[0 .. D] (lengthscales, output scale); tb holds the packed exponent operands
+gp_status contract_tc(const Prob& pb, const void* Xs, const TcBufs& tb, const TcGradBufs& gb,
+                      const float* A, int64_t lda, const float* B, int64_t ldb,
+                      const double* wts, int t, double* gout, cudaStream_t st);
+// gout = sum_a sum_c w_c A[a,c] B[a,c]  (the noise entry: dK_hat/dsigma^2 = I)
+template <class T>
+gp_status contract_noise(const Prob& pb, const void* A, int64_t lda, const void* B, int64_t ldb,
+                         const double* wts, int t, double* part, unsigned* counter, double* gout,
+                         cudaStream_t st);
+
 // ---- pivoted Cholesky (pivchol.cu) ----------------------------------------------
 struct PivBufs {
   double* dres;      // n: residual diagonal, -1 marks chosen rows
@@ -130,9 +156,10 @@ struct MvmOp {
   virtual ~MvmOp() {}
 };
 // Optional CUDA-event timing of the products issued by cg_solve.
+// Phase 0: kernel-matrix products; phase 1: the gradient contraction.
 bool mvm_timing_enabled();
-void mvm_timing_begin(cudaStream_t st);
-void mvm_timing_end(cudaStream_t st);
+void mvm_timing_begin(cudaStream_t st, int phase = 0);
+void mvm_timing_end(cudaStream_t st, int phase = 0);
 template <class T>
 gp_status cg_solve(const Prob& pb, MvmOp& mvm, const T* L, int64_t ldl, int k,
                    const double* Cinv, const T* B, int64_t ldb, int t,

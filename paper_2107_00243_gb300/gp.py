@@ -91,6 +91,8 @@ def load():
         "gp_measure_peaks": (i32, [vp, ctypes.POINTER(ctypes.c_double), vp]),
         "gp_mvm_timing": (None, [i32]),
         "gp_mvm_timing_read": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
+        "gp_phase_timing_read": (i32, [i32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -164,7 +166,7 @@ class Problem:
         return ctypes.byref(self._c)
 
 
-OPT_SPLIT_P, OPT_AUTO_SPLIT, OPT_FAST_ONLY = 1, 2, 4
+OPT_SPLIT_P, OPT_AUTO_SPLIT, OPT_FAST_ONLY, OPT_SIMT_GRAD = 1, 2, 4, 8
 
 
 def opts(cg_tol=1e-6, max_iter=200, recompute_every=0, seed=0, pivchol_tol=0.0, check_every=0,
@@ -468,4 +470,14 @@ def mvm_timing_read():
     ms = ctypes.c_double(0.0)
     cnt = ctypes.c_int64(0)
     _check("gp_mvm_timing_read", load().gp_mvm_timing_read(ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def phase_timing_read(phase):
+    """(total ms, brackets) of a timed phase since the last read: 0 = kernel-matrix
+    products, 1 = the gradient contraction (one bracket per evaluation)."""
+    ms = ctypes.c_double(0.0)
+    cnt = ctypes.c_int64(0)
+    _check("gp_phase_timing_read",
+           load().gp_phase_timing_read(int(phase), ctypes.byref(ms), ctypes.byref(cnt)))
     return ms.value, cnt.value
