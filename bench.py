@@ -170,32 +170,26 @@ def _barrier(dist):
 # CG iterations (max over the 33 columns) this workload needs at tol 1e-2, measured
 # with the FP32 GPU form; used only to scale the oracle's timing in the reference arm.
 WORKLOAD_MAX_ITERS = 323
-SAMPLE_ROWS = 250
+SUBSAMPLE_N = 2000
 
 
-def oracle_product_seconds(reps=3, rows=SAMPLE_ROWS):
-    """The FP64 oracle's kernel product (K + sigma^2 I) V on the full n = 1e5 workload,
-    timed on a sample of `rows` rows and scaled to all n rows: median seconds per
-    full product, the raw sample times, and the threads its BLAS used."""
-    import numpy as np
-    from oracle import kernels
-    from paper_2107_00243_gb300 import workloads
-    p = workloads.c3_rbf_ard_1e5()
-    V = np.random.default_rng(0).standard_normal((p.n, p.n_probes + 1))
-    idx = np.random.default_rng(1).choice(p.n, rows, replace=False)
-    times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        Kr = kernels.kernel_block(p.kind, p.X[idx], p.X, p.theta, p.ard)
-        _ = Kr @ V + p.theta[-1] * V[idx]
-        times.append(time.perf_counter() - t0)
+def _cpu_info():
+    """CPU model, logical cores and the threads the oracle's BLAS uses."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
     try:
         from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
     except Exception:
-        cores = os.cpu_count() or 1
-    scale = p.n / rows
-    return statistics.median(times) * scale, times, cores
+        threads = os.cpu_count() or 1
+    return {"cpu_model": model, "nproc": os.cpu_count(), "threads": threads}
 
 
 def products_per_eval(max_iters, recompute_every=25, n_hyper=18):
@@ -205,29 +199,67 @@ def products_per_eval(max_iters, recompute_every=25, n_hyper=18):
     return max_iters + math.ceil(max_iters / recompute_every) + 2 * (n_hyper - 1)
 
 
+def oracle_subsample_seconds(n_sub=SUBSAMPLE_N):
+    """The FP64 oracle estimator (MLL and gradient, Alg. 1 + Alg. 2) end to end on an
+    n_sub-point subsample of the n = 1e5 workload (same d, kernel, k, l, tol): seconds
+    and the largest CG iteration count."""
+    from oracle import estimator
+    from paper_2107_00243_gb300 import workloads
+    p = workloads.subsample(workloads.c3_rbf_ard_1e5(n=20000), n_sub)
+    t0 = time.perf_counter()
+    r = estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, p.k, p.n_probes, p.tol,
+                               p.max_iter, seed=p.seed, recompute_every=p.recompute_every)
+    return time.perf_counter() - t0, int(max(r["iters"]))
+
+
+def extrapolate(t_sub, m_sub, m_full, n_full=100000, n_sub=SUBSAMPLE_N, n_hyper=18):
+    """Scale a subsample's time to the full workload: (n / n_sub)^2 per kernel product,
+    times the ratio of product-equivalents per evaluation at the two sizes."""
+    return (t_sub * (n_full / n_sub) ** 2 * products_per_eval(m_full, 25, n_hyper)
+            / products_per_eval(m_sub, 25, n_hyper))
+
+
+def oracle_small_configs():
+    """Timed, not scaled: the oracle estimator and the exact dense-Cholesky MLL and
+    gradient on the small RBF workload (n = 1,000, d = 3, FP64)."""
+    from oracle import estimator, exact
+    from paper_2107_00243_gb300 import workloads
+    p = workloads.c1_small_rbf()
+    t0 = time.perf_counter()
+    estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, p.k, p.n_probes, p.tol,
+                           p.max_iter, seed=p.seed)
+    t1 = time.perf_counter()
+    exact.exact_mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard)
+    t2 = time.perf_counter()
+    return {"small_rbf_n1000_estimator_s": t1 - t0, "small_rbf_n1000_exact_s": t2 - t1}
+
+
 def run_reference(args, rank, ws, dist):
     if rank != 0:
         _barrier(dist)
         return
-    nprod = products_per_eval(WORKLOAD_MAX_ITERS)
-    per_step = []
-    cores = os.cpu_count() or 1
+    sample_times, m_sub = [], 0
     for i in range(args.warmup + args.steps):
-        t_prod, _, cores = oracle_product_seconds(reps=1)
+        t_sub, m_sub = oracle_subsample_seconds()
         if i >= args.warmup:
-            per_step.append(t_prod * nprod)
-    value = statistics.mean(per_step)
-    sample = (f"FP64 oracle (numpy) kernel product on {SAMPLE_ROWS} sampled rows of the "
-              f"n=1e5 workload (t=33), scaled to all rows and multiplied by {nprod} "
-              f"product-equivalents per evaluation ({WORKLOAD_MAX_ITERS} CG iterations, "
-              "residual recomputes every 25, 2 x 17 derivative passes)")
+            sample_times.append(t_sub)
+    t_mean = statistics.mean(sample_times)
+    value = extrapolate(t_mean, m_sub, WORKLOAD_MAX_ITERS)
+    info = _cpu_info()
+    sample = (f"extrapolated: each of the {args.steps} timed steps ran the FP64 oracle "
+              f"estimator (MLL + gradient) end to end on a {SUBSAMPLE_N}-point subsample of "
+              f"the n=1e5 workload ({t_mean:.2f} s mean, {m_sub} CG iterations); the value "
+              f"scales that by (1e5/{SUBSAMPLE_N})^2 and by the product-equivalents per "
+              f"evaluation ({WORKLOAD_MAX_ITERS} CG iterations at n=1e5)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "fp64-cpu-oracle"},
-            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "extrapolated": True, "steps_run": len(sample_times),
+            "sample_s_per_step": sample_times,
+            "cpu_baseline": {"value": value, "unit": "s", "cores": info["threads"],
+                             "kind": "oracle", "sample": sample, **info},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -449,8 +481,9 @@ def main():
             total += e0.elapsed_time(e1) / 1e3
         launches = gp.launch_count() - l0
         mvm_ms, mvm_n = gp.mvm_timing_read()
+        con = gp.phase_timing_read(1)
         gp.mvm_timing(False)
-        return total, launches, mvm_ms, mvm_n
+        return total, launches, mvm_ms, mvm_n, con
 
     prob, wsp, out, iout, y = setup(prec)
     for _ in range(args.warmup):
@@ -462,8 +495,8 @@ def main():
     _barrier(dist)
     torch.cuda.synchronize()
     sampler.start()
-    total, launches, mvm_ms, mvm_n = timed_steps(prob, wsp, out, iout, y, args.steps,
-                                                 measure_mvm=True)
+    total, launches, mvm_ms, mvm_n, (con_ms, con_n) = timed_steps(
+        prob, wsp, out, iout, y, args.steps, measure_mvm=True)
     clocks = sampler.stop()
     torch.cuda.synchronize()
     _barrier(dist)
@@ -478,7 +511,7 @@ def main():
         # one warm-up evaluation: the plain FP32 form runs for tens of seconds
         gp.gp_mll_and_grad(prob32, y32, p.k, p.n_probes, o, workspace=wsp32, out=out32,
                            iout=iout32)
-        tot32, _, _, _ = timed_steps(prob32, wsp32, out32, iout32, y32, args.fp32_steps)
+        tot32, _, _, _, _ = timed_steps(prob32, wsp32, out32, iout32, y32, args.fp32_steps)
         fp32_value = _max_over_ranks(tot32, dist) / (args.fp32_steps * ws)
         fp32_mll = gp.unpack(out32, iout32, prob32.p, p.n_probes, p.k)["mll"]
         del wsp32, out32, iout32
@@ -545,16 +578,45 @@ def main():
                        "frac": ex2_rate / ex2_peak,
                        "peak_source": "ex2.approx.f32, measured (profiles/unit_peaks_gb300.txt)"}
 
+    # the gradient contraction (Alg. 2's O(n^2) pass): algorithmic FLOPs per kernel
+    # entry 2 d (distance) + 2 t (m_ab) + 2 (2 d + 1) ([1, x, x^2] contraction); the
+    # tensor-core form executes 2 kx + 2 tm + 4 nr per entry (hi / lo operands, padding)
+    contraction = None
+    if con_n:
+        con_s = (con_ms / 1e3) / con_n
+        cflops = float(p.n) ** 2 * (2 * p.d + 2 * t + 2 * (2 * p.d + 1))
+        con_ach = cflops / con_s / 1e12
+        kx = 64 if 3 * (p.d + 2) <= 64 else 128
+        tm = (t + 15) // 16 * 16
+        nr = (4 + 4 * p.d + 15) // 16 * 16
+        executed = 2 * kx + 2 * tm + 4 * nr
+        bf = peaks.get("bf16_tflops_sustained", 1700.0)
+        contraction = {
+            "kernel": "grad_tc_kernel" if prec == gp.BF16 else "contract_kernel",
+            "ms_per_eval": con_s * 1e3, "evals_timed": con_n,
+            "bound": "tensor" if prec == gp.BF16 else "alu",
+            "achieved": con_ach, "unit": "TFLOP/s",
+            "peak": bf if prec == gp.BF16 else roof["peak"],
+            "frac": con_ach / (bf if prec == gp.BF16 else roof["peak"]),
+            "algorithmic_flops_per_entry": 2 * p.d + 2 * t + 2 * (2 * p.d + 1),
+            "executed_tensor_flops_per_entry": executed if prec == gp.BF16 else None,
+            "peak_source": peak_note if prec == gp.BF16 else roof["peak_source"]}
+
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        t_prod, times, cores = oracle_product_seconds(reps=3)
-        nprod = products_per_eval(int(max(res["iters"])), p.recompute_every, prob.p)
-        cpu = {"value": t_prod * nprod, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": (f"FP64 oracle kernel product on {SAMPLE_ROWS} sampled rows of the same "
-                          f"workload (median of 3: {', '.join(f'{x:.2f}' for x in times)} s), "
-                          f"scaled to all 1e5 rows and multiplied by {nprod} product-equivalents "
-                          f"per evaluation (max CG iterations {int(max(res['iters']))} of this "
-                          "run, residual recomputes, 2 x (p-1) derivative passes)")}
+        t_sub, m_sub = oracle_subsample_seconds()
+        m_full = int(max(res["iters"]))
+        small = oracle_small_configs()
+        info = _cpu_info()
+        cpu = {"value": extrapolate(t_sub, m_sub, m_full, p.n, SUBSAMPLE_N, prob.p),
+               "unit": "s", "cores": info["threads"], "kind": "oracle", "extrapolated": True,
+               "sample": (f"FP64 oracle estimator (MLL + gradient) end to end on a "
+                          f"{SUBSAMPLE_N}-point subsample of the same workload ({t_sub:.2f} s, "
+                          f"{m_sub} CG iterations), scaled by (1e5/{SUBSAMPLE_N})^2 and by the "
+                          f"product-equivalents per evaluation ({m_full} CG iterations in this "
+                          "run, residual recomputes, 2 x (p-1) derivative passes)"),
+               "timed": {"subsample_estimator_s": t_sub, "subsample_n": SUBSAMPLE_N, **small},
+               **info}
 
     dtype = {gp.FP32: "f32", gp.BF16: "bf16", gp.TF32: "tf32"}[prec]
     line = {
@@ -569,7 +631,7 @@ def main():
         "speedup_vs_fp32_form": (fp32_value / value) if fp32_value else None,
         "fp32_form_mll": fp32_mll,
         "iters": res["iters"].tolist(), "mll": res["mll"], "status": res["status"],
-        "roofline": roof, "cpu_baseline": cpu,
+        "roofline": roof, "contraction": contraction, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -68,3 +68,17 @@ def test_products_per_eval(bench):
     # 334 iterations, a recompute every 25 (14), and 2 (18 - 1) derivative passes
     assert bench.products_per_eval(334, 25, 18) == 334 + 14 + 34
     assert bench.products_per_eval(25, 25, 1) == 25 + 1
+
+
+def test_extrapolation_scales_by_size_and_products(bench):
+    """The oracle's subsample time scales with n^2 per product and with the ratio of
+    product-equivalents per evaluation."""
+    t = bench.extrapolate(2.0, 20, 300, n_full=4000, n_sub=2000, n_hyper=18)
+    ratio = bench.products_per_eval(300, 25, 18) / bench.products_per_eval(20, 25, 18)
+    assert t == pytest.approx(2.0 * 4.0 * ratio)
+    assert bench.extrapolate(1.0, 50, 50, n_full=2000, n_sub=2000) == pytest.approx(1.0)
+
+
+def test_cpu_info_reports_cores_and_threads(bench):
+    info = bench._cpu_info()
+    assert info["nproc"] >= 1 and info["threads"] >= 1
