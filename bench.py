@@ -314,7 +314,18 @@ def run_case(args):
     gen = torch.Generator(device="cuda").manual_seed(0)
     V = torch.randn(p.n, t, device="cuda", generator=gen)
     times = []
-    if args.case == "kmvm":
+    if args.case == "grad":
+        # the estimator with CG capped at 4 iterations: one gradient contraction per call
+        o = gp.opts(cg_tol=p.tol, max_iter=4, recompute_every=p.recompute_every, seed=0,
+                    flags=gp.OPT_FAST_ONLY)
+        gp.mvm_timing(True)
+        for _ in range(args.reps):
+            gp.phase_timing_read(1)
+            gp.gp_mll_and_grad(prob, p.y, p.k, p.n_probes, o)
+            torch.cuda.synchronize()
+            times.append(gp.phase_timing_read(1)[0])
+        gp.mvm_timing(False)
+    elif args.case == "kmvm":
         for _ in range(args.reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -418,10 +429,11 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=1,
                     help="timed steps of the plain FP32 form when --precision is mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg", "batched", "peaks"],
+    ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg", "grad", "batched", "peaks"],
                     default="estimator",
-                    help="kmvm / mbcg: time only the kernel product or a short CG call on a "
-                         "smaller instance of the workload (for profiling)")
+                    help="kmvm / mbcg / grad: time only the kernel product, a short CG call "
+                         "or the gradient contraction on an instance of the workload (for "
+                         "profiling)")
     ap.add_argument("--n", type=int, default=None, help="instance size for --case")
     ap.add_argument("--reps", type=int, default=3, help="calls for --case")
     args = ap.parse_args()

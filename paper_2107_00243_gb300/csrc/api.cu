@@ -264,6 +264,37 @@ SideStream& side_stream(int i = 0) {
   return s;
 }
 
+// Hyperparameters must be finite and positive (lengthscales, output scale, noise).
+__global__ void theta_check(const double* theta, int p, int* status) {
+  const int q = threadIdx.x;
+  if (q >= p) return;
+  const double v = theta[q];
+  if (!(v > 0.0) || !isfinite(v)) raise_status(status, GP_ERR_INVALID_ARG);
+}
+
+// Runs theta_check on `status` (zeroed first).  Outside stream capture the result is
+// read back: an invalid theta returns GP_ERR_INVALID_ARG (also stored in *iout, when
+// given) before anything else runs.  Under capture the check stays on the device and
+// the evaluation's status word carries the error.
+gp_status check_theta(const Prob& pb, int* status, int* iout, cudaStream_t st) {
+  GP_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  theta_check<<<1, 64, 0, st>>>(pb.theta, pb.p, status);
+  GP_LAUNCH_CHECK();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GP_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap == cudaStreamCaptureStatusActive) return GP_OK;
+  int h = 0;
+  GP_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h < 0) {
+    if (iout) GP_CUDA_TRY(cudaMemcpyAsync(iout + GP_IOUT_STATUS, status, sizeof(int),
+                                          cudaMemcpyDeviceToDevice, st));
+    set_error("theta must be finite and positive (lengthscales, output scale, noise)");
+    return GP_ERR_INVALID_ARG;
+  }
+  return GP_OK;
+}
+
 // ---- split mode of the tensor-core product (GP_OPT_*) ----------------------------------
 __global__ void set_int_kernel(int* p, int v) { *p = v; }
 
@@ -428,8 +459,8 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   GP_CUDA_TRY(cudaMemsetAsync(P.counter, 0, 4 * sizeof(unsigned), st));
   GP_CUDA_TRY(cudaMemsetAsync(P.piv.b.counter, 0, 4 * sizeof(unsigned), st));
   GP_CUDA_TRY(cudaMemsetAsync(P.cg.counter, 0, 4 * sizeof(unsigned), st));
-  GP_CUDA_TRY(cudaMemsetAsync(P.cg.status, 0, sizeof(int), st));
   GP_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * GP_OUT_LEN(pb.p, nl), st));
+  GP_TRY(check_theta(pb, P.cg.status, iout, st));
 
   // S1: scaled inputs
   GP_TRY(run_prep<T>(pb, P.mvm.prep, st));
@@ -528,6 +559,8 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
     return (gp_status)herr[0];
   }
   if (hstat < 0) return (gp_status)hstat;
+  const gp_status warn = hstat > 0 ? (gp_status)hstat
+                                   : (hrank < k ? GP_WARN_RANK_DEFICIENT : GP_OK);
   // Mixed precision in fast mode: estimate the first-order change of the MLL had the
   // product carried k(r)/s to 22 bits (split mode) instead of 11; beyond the 5e-3
   // mixed-precision bound, evaluate again in split mode.  Where the change matters,
@@ -575,8 +608,7 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
       if (r != GP_OK) return r;
     }
   }
-  if (hrank < k) return GP_WARN_RANK_DEFICIENT;
-  return GP_OK;
+  return warn;
 }
 
 template <class T>
@@ -822,7 +854,7 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
   plan_cg<T>(A, pb, k, t, o.max_iter, cb);
   (void)ws_bytes;
   GP_CUDA_TRY(cudaMemsetAsync(cb.counter, 0, 4 * sizeof(unsigned), st));
-  GP_CUDA_TRY(cudaMemsetAsync(cb.status, 0, sizeof(int), st));
+  GP_TRY(check_theta(pb, cb.status, nullptr, st));
   GP_CUDA_TRY(cudaMemsetAsync(cb.alpha, 0, sizeof(double) * (size_t)t * o.max_iter, st));
   GP_CUDA_TRY(cudaMemsetAsync(cb.beta, 0, sizeof(double) * (size_t)t * o.max_iter, st));
   GP_TRY(run_prep<T>(pb, mp.prep, st));
@@ -871,8 +903,7 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
     set_error("tensor-core product gave up waiting (site %d)", herr[1]);
     return (gp_status)herr[0];
   }
-  if (hs < 0) return (gp_status)hs;
-  return GP_OK;
+  return (gp_status)hs;   // 0, a warning (> 0) or an error (< 0)
 }
 }  // namespace
 }  // namespace gp

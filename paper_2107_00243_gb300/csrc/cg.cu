@@ -430,7 +430,7 @@ __global__ void rho_combine(int t, int nb, int mode, int j, int max_iter, Dev<T>
         continue;
       }
       double be = s / g.rho[c];
-      if (!isfinite(be)) { *g.status = GP_ERR_NUMERIC; be = 0.0; }
+      if (!isfinite(be)) { raise_status(g.status, GP_ERR_NUMERIC); be = 0.0; }
       g.beta[(int64_t)c * max_iter + j] = be;
       g.rho[c] = s;
     }
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kThreads) cg_alpha(int64_t n, int t, int j, in
       if (!(pq > 0.0) || !isfinite(al)) {
         // breakdown: the operator is not positive definite in this precision (or
         // the iterates overflowed); the column stops with the j steps it has
-        *g.status = GP_ERR_NUMERIC;
+        raise_status(g.status, GP_ERR_NUMERIC);
         g.alpha[(int64_t)c * max_iter + j] = 0.0;
         g.active[c] = 0;
         g.iters[c] = j;
@@ -488,21 +488,26 @@ __global__ void __launch_bounds__(kThreads) cg_alpha(int64_t n, int t, int j, in
 
 __device__ void decide(int t, int j, const double* rnorm2_part, int nb, double tol2,
                        int use_caps, int max_iter, int* active, const int* caps, int* iters,
-                       const double* bnorm2, int* n_active) {
+                       const double* bnorm2, int* n_active, int* status) {
   __shared__ int cnt;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   for (int c = warp; c < t; c += blockDim.x >> 5) {
     if (!active[c]) continue;
-    bool stop;
+    bool stop, capped = false;
     if (use_caps) {
       stop = (j + 1) >= caps[c];
     } else {
       const double s = warp_col_sum(rnorm2_part, nb, c);
-      stop = (s <= tol2 * bnorm2[c]) || (j + 1 >= max_iter);
+      const bool conv = s <= tol2 * bnorm2[c];
+      capped = !conv && (j + 1 >= max_iter);
+      stop = conv || capped;
     }
     if (lane != 0) continue;
+    // the iteration cap ended a column above the tolerance: results are written, with a
+    // warning (with per-column caps from the caller the stop is deliberate)
+    if (capped) raise_status(status, GP_WARN_NOT_CONVERGED);
     if (stop) {
       active[c] = 0;
       iters[c] = j + 1;
@@ -545,7 +550,7 @@ __global__ void __launch_bounds__(kThreads) cg_update(int64_t n, int t, int j, i
   if (recompute) return;
   if (last_block_arrived(g.counter))
     decide(t, j, g.part, nb, tol2, use_caps, max_iter, g.active, g.caps, g.iters, g.bnorm2,
-           g.n_active);
+           g.n_active, g.status);
 }
 
 // r = b - K_hat x (Q holds K_hat x), ||r||^2, stopping decision.
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(kThreads) cg_resid(int64_t n, int t, int j, in
   }
   if (last_block_arrived(g.counter))
     decide(t, j, g.part, nb, tol2, use_caps, max_iter, g.active, g.caps, g.iters, g.bnorm2,
-           g.n_active);
+           g.n_active, g.status);
 }
 
 // p = z + beta_j p for active columns.

@@ -205,6 +205,18 @@ __device__ __forceinline__ bool last_block_arrived(unsigned int* counter) {
   return last;
 }
 
+// Device status word: 0 = fine, > 0 a warning, < 0 an error.  An error replaces 0 or a
+// warning, and the first error stays (a later failure is usually a consequence of it);
+// a warning replaces only 0.
+__device__ __forceinline__ void raise_status(int* status, int code) {
+  int old = *reinterpret_cast<volatile int*>(status);
+  while (old >= 0 && (code < 0 || old == 0) && old != code) {
+    const int prev = atomicCAS(status, old, code);
+    if (prev == old) break;
+    old = prev;
+  }
+}
+
 __device__ __forceinline__ void load_hyper(const double* theta, int d, int ard, Hyper& h) {
   int D = ard ? d : 1;
   for (int j = 0; j < d; ++j) {

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kQuadThreads) logquad_kernel(
     double sum = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
     gamma[blockIdx.x] = rho0[c] * kQuadStep * sum;
-    if (bad) atomicExch(status, GP_ERR_NOT_SPD);
+    if (bad) raise_status(status, GP_ERR_NOT_SPD);
   }
 }
 

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(1024) core_cholesky(int k, const double* __res
   if (tid == 0) {
     // log det P_hat = (n - k) log s2 + log det C   (determinant lemma)
     *logdetP = (double)(n - k) * log(s2) + 2.0 * ld;
-    if (bad) *status = GP_ERR_NOT_SPD;
+    if (bad) raise_status(status, GP_ERR_NOT_SPD);
   }
 }
 

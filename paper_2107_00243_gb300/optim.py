@@ -223,7 +223,8 @@ def lbfgs_fit(problem, y, theta0, k, n_probes, opts, max_iter=50, validation=Non
         problem.set_theta(theta)
         st, out, iout = gp.gp_mll_and_grad(problem, y, k, n_probes, opts, workspace=ws)
         r = gp.unpack(out, iout, problem.p, n_probes, k)
-        if st < 0 or r["status"] != 0 or not np.isfinite(r["mll"]):
+        # warnings (> 0: CG capped, rank-deficient preconditioner) still give results
+        if st < 0 or r["status"] < 0 or not np.isfinite(r["mll"]):
             return math.inf, np.zeros_like(phi)
         # d(-mll)/d(log theta) = -theta * dmll/dtheta
         return -float(r["mll"]), -theta * np.asarray(r["grad"], dtype=np.float64)
