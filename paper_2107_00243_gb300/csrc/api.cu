@@ -171,10 +171,11 @@ struct SimtMvm : MvmOp {
 struct TcMvm : MvmOp {
   Prob pb;
   TcBufs tb;
+  int mode = 0;   // 0 fast, 1 split, 2 the device's split flag decides (kmvm_tc)
   gp_status apply(const void* V, int64_t ldv, int t, void* W, int64_t ldw, const int* gate,
                   cudaStream_t st) override {
     return kmvm_tc(pb, tb, static_cast<const float*>(V), ldv, t, static_cast<float*>(W), ldw,
-                   gate, st);
+                   gate, mode, st);
   }
 };
 
@@ -340,6 +341,13 @@ gp_status tc_split_setup(const Prob& pb, MvmOp& op, const TcBufs& tb, T* ones, T
   return GP_OK;
 }
 
+// The product's operand form for CG under these options (TcMvm::mode).
+inline int split_mode_of(const gp_opts& o) {
+  if (o.flags & GP_OPT_SPLIT_P) return 1;
+  if (o.flags & GP_OPT_AUTO_SPLIT) return 2;
+  return 0;
+}
+
 // After an eager CG call that broke down in fast mode: true (and split mode set)
 // when CG should run again.
 inline bool tc_retry_split(const TcBufs& tb, int host_status, cudaStream_t st) {
@@ -483,9 +491,11 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
     op.pb = pb;
     op.tb = P.mvm.tc;
     GP_TRY(tc_split_setup<T>(pb, op, P.mvm.tc, P.cg.Q, P.cg.R, o, st));
+    op.mode = split_mode_of(o);
     GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o, P.cg,
                        P.PinvB, pb.n, &host_status, st));
     if (!(o.flags & GP_OPT_FAST_ONLY) && tc_retry_split(P.mvm.tc, host_status, st)) {
+      op.mode = 1;
       GP_CUDA_TRY(cudaMemsetAsync(P.cg.status, 0, sizeof(int), st));
       GP_TRY(cg_solve<T>(pb, op, P.L, pb.n, k, P.core.Cinv, P.B, pb.n, t, iters_override, o,
                          P.cg, P.PinvB, pb.n, &host_status, st));
@@ -578,6 +588,7 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
       op.tb = P.mvm.tc;
       GP_TRY(op.apply(P.cg.X, pb.n, t, P.cg.Q, pb.n, nullptr, st));           // fast
       set_int_kernel<<<1, 1, 0, st>>>(P.mvm.tc.err + 2, 1);
+      op.mode = 1;
       GP_LAUNCH_CHECK();
       GP_TRY(op.apply(P.cg.X, pb.n, t, P.cg.R, pb.n, nullptr, st));           // split
       set_int_kernel<<<1, 1, 0, st>>>(P.mvm.tc.err + 2, 0);
@@ -869,9 +880,11 @@ gp_status mbcg_impl(const Prob& pb, const T* L, int64_t ldl, int k, const T* B, 
     op.pb = pb;
     op.tb = mp.tc;
     GP_TRY(tc_split_setup<T>(pb, op, mp.tc, cb.Q, cb.R, o, st));
+    op.mode = split_mode_of(o);
     GP_TRY(cg_solve<T>(pb, op, L, ldl, k, cp.Cinv, B, ldb, t, iters_override, o, cb, PinvB, ldx,
                        &host_status, st));
     if (!(o.flags & GP_OPT_FAST_ONLY) && tc_retry_split(mp.tc, host_status, st)) {
+      op.mode = 1;
       GP_CUDA_TRY(cudaMemsetAsync(cb.status, 0, sizeof(int), st));
       GP_TRY(cg_solve<T>(pb, op, L, ldl, k, cp.Cinv, B, ldb, t, iters_override, o, cb, PinvB,
                          ldx, &host_status, st));
@@ -1277,5 +1290,5 @@ extern "C" gp_status gp_tc_exponent_tile(const gp_problem* prob, const void* V, 
   GP_CUDA_TRY(cudaMemsetAsync(P.tc.err, 0, kTcErrInts * sizeof(int), st));
   GP_TRY(tc_prepare_inputs(pb, P.prep.pr.Xs, P.tc, st));
   return kmvm_tc_debug(pb, P.tc, static_cast<const float*>(V), ldv, t, static_cast<float*>(W),
-                       ldw, nullptr, S_out, st);
+                       ldw, nullptr, S_out, 0, st);
 }

@@ -9,9 +9,11 @@
 //
 //   GEMM_S  S = A_I B_J^T, the exponent GEMM of the kernel product (BF16 hi / lo
 //           operands, FP32 in TMEM): S = -c r^2 / 2 (c = log2 e for RBF, 1 for Matern).
-//   GEMM_M  M = A'_I B'_J^T (FP16, K = t padded to 16, FP32 in TMEM), with
-//           A'_ac = w_c A_ac 2^e_c and B'_bc = B_bc 2^(E - e_c): power-of-two column
-//           scales put max |A'_c| in [2^13, 2^14) and bound |M| = 2^E |m| < 2^14.
+//   GEMM_M  M = A'_I B'_J^T (FP32 in TMEM), with A'_ac = w_c A_ac 2^e_c and
+//           B'_bc = B_bc 2^(E - e_c): power-of-two column scales put max |A'_c| in
+//           [2^13, 2^14) and bound |M| = 2^E |m| < 2^14.  Both operands are FP16 hi + lo
+//           pairs and K holds the three segments [A'_hi | A'_hi | A'_lo] .
+//           [B'_hi | B'_lo | B'_hi] (K = 3 t padded to 16): ~22 bits in M.
 //   epilogue  from S: k/s and fac/s; H = (fac/s) M, rounded to FP16 hi + lo (22
 //           significant bits) and written to TMEM; the scale term sum (k/s) M is
 //           summed in registers.
@@ -28,6 +30,9 @@
 // Matern-3/2 and Matern-5/2 workloads, and on an isotropic Matern-3/2 problem, puts
 // the gradient entries within 1.2e-4 of the exact contraction (relative to
 // 1/2 (|quad_p| + |trace_p|)); with FP16 H alone the isotropic case reaches 5e-3.
+// M carries 22 bits as well: with single FP16 operands the output-scale entry of an
+// ill-conditioned problem (lambda_max / sigma^2 ~ 1.7e5) was 8.6e-3 off the oracle,
+// against 1.2e-3 for the FP32 CUDA-core contraction on the same CG solutions.
 //
 // Roles of a CTA (persistent over (row tile, column chunk) work units):
 //   warp 0      producer: bulk copies of the unit's row tiles (exponent A form, M
@@ -68,13 +73,15 @@ constexpr size_t kSmemCap = 220 * 1024;
 struct GradArgs {
   const __nv_bfloat16* xa;   // exponent operand tiles, A form (BM x kx each)
   const __nv_bfloat16* xb;   // exponent operand tiles, B form
+  const __nv_bfloat16* xa3;  // the product's three-part split-mode operands (kx3 wide)
+  const __nv_bfloat16* xb3;
   const __half* ma;          // M operand tiles A' (BM x tm each)
   const __half* mb;          // M operand tiles B'
   const __half* xr;          // coordinate tiles (nr x BN each)
   const float* Xs;           // n x d scaled inputs (row combination)
   double* part;              // gridDim.x x kPartStride
-  int n, ntiles, nchunks, tiles_per_chunk, kx, tm, nr, d, kind, ns;
-  int* err;                  // err[0] status, err[1] the wait that gave up
+  int n, ntiles, nchunks, tiles_per_chunk, kx, kx3, kx3_ok, tm, nr, d, kind, ns;
+  int* err;                  // err[0] status, err[1] the wait that gave up, err[2] split
 };
 
 struct __align__(8) Bars {
@@ -136,7 +143,12 @@ __device__ __forceinline__ float h_from_sm(const uint32_t (&sv)[32], const uint3
 __global__ void __launch_bounds__(kThreads, 1) grad_tc_kernel(GradArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kx = g.kx, tm = g.tm, nr = g.nr, ns = g.ns;
+  // in split mode k(r) comes from the same three-part exponent operands as the CG
+  // products used (when shared memory was sized for them: kx3_ok)
+  const bool wide = g.err[2] != 0 && g.kx3_ok;
+  const int kx = wide ? g.kx3 : g.kx, tm = g.tm, nr = g.nr, ns = g.ns;
+  const __nv_bfloat16* xa = wide ? g.xa3 : g.xa;
+  const __nv_bfloat16* xb = wide ? g.xb3 : g.xb;
   const uint32_t a_bytes = BM * kx * 2, am_bytes = BM * tm * 2;
   const uint32_t b_bytes = BN * kx * 2, bm_bytes = BN * tm * 2, xr_bytes = (uint32_t)nr * BN * 2;
   const uint32_t stage_bytes = b_bytes + bm_bytes + xr_bytes;
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_tc_kernel(GradArgs g) {
         // the previous unit's GEMM_S / GEMM_M are done with the row tiles
         if (!mbar_wait(smem_u32(&bars->a_free), (k & 1u) ^ 1u, abort, g.err, 41)) break;
         mbar_expect_tx(smem_u32(&bars->a_full), a_bytes + am_bytes);
-        bulk_g2s(smem_u32(sA), reinterpret_cast<const unsigned char*>(g.xa) + (size_t)rt * a_bytes,
+        bulk_g2s(smem_u32(sA), reinterpret_cast<const unsigned char*>(xa) + (size_t)rt * a_bytes,
                  a_bytes, smem_u32(&bars->a_full));
         bulk_g2s(smem_u32(sAM),
                  reinterpret_cast<const unsigned char*>(g.ma) + (size_t)rt * am_bytes, am_bytes,
@@ -207,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_tc_kernel(GradArgs g) {
           const uint32_t fb = smem_u32(&bars->full[st]);
           unsigned char* dst = sStage + (size_t)st * stage_bytes;
           mbar_expect_tx(fb, stage_bytes);
-          bulk_g2s(smem_u32(dst), reinterpret_cast<const unsigned char*>(g.xb) + (size_t)j * b_bytes,
+          bulk_g2s(smem_u32(dst), reinterpret_cast<const unsigned char*>(xb) + (size_t)j * b_bytes,
                    b_bytes, fb);
           bulk_g2s(smem_u32(dst + b_bytes),
                    reinterpret_cast<const unsigned char*>(g.mb) + (size_t)j * bm_bytes, bm_bytes, fb);
@@ -475,7 +487,10 @@ __global__ void mscale_kernel(int t, const int* __restrict__ cmax, const double*
   *inv2E = ldexp(1.0, -E);
 }
 
-// A' and B' (FP16) in tiles of BM rows x tm columns, canonical K-major layout.
+// A' and B' as FP16 hi / lo pairs in tiles of BM rows x tm columns, canonical K-major
+// layout: K index k = s t + c (segment s < 3, column c < t) holds
+//   A: [hi, hi, lo][s] of A'_rc,   B: [hi, lo, hi][s] of B'_rc,
+// so that sum_k A_k B_k = sum_c (hi hi + hi lo + lo hi); zero beyond 3 t.
 __global__ void pack_m_kernel(int n, int ntiles, int t, int tm, const float* __restrict__ A,
                               int64_t lda, const float* __restrict__ B, int64_t ldb,
                               const float* __restrict__ mscale, __half* __restrict__ ma,
@@ -483,11 +498,18 @@ __global__ void pack_m_kernel(int n, int ntiles, int t, int tm, const float* __r
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)ntiles * BM * tm) return;
   const int r = (int)(e % ((int64_t)ntiles * BM));
-  const int c = (int)(e / ((int64_t)ntiles * BM));
-  const bool v = r < n && c < t;
-  const float a = v ? A[r + (int64_t)c * lda] * mscale[c] : 0.f;
-  const float b = v ? B[r + (int64_t)c * ldb] * mscale[kMaxTC + c] : 0.f;
-  const size_t off = (size_t)(r / BM) * BM * tm * 2 + tile_off(r % BM, c, tm);
+  const int k = (int)(e / ((int64_t)ntiles * BM));
+  const int seg = k / t, c = k % t;
+  const bool v = r < n && seg < 3;
+  float a = 0.f, b = 0.f;
+  if (v) {
+    const float av = A[r + (int64_t)c * lda] * mscale[c];
+    const float bv = B[r + (int64_t)c * ldb] * mscale[kMaxTC + c];
+    const float ah = __half2float(__float2half_rn(av)), bh = __half2float(__float2half_rn(bv));
+    a = seg == 2 ? av - ah : ah;
+    b = seg == 1 ? bv - bh : bh;
+  }
+  const size_t off = (size_t)(r / BM) * BM * tm * 2 + tile_off(r % BM, k, tm);
   *reinterpret_cast<__half*>(reinterpret_cast<unsigned char*>(ma) + off) = __float2half_rn(a);
   *reinterpret_cast<__half*>(reinterpret_cast<unsigned char*>(mb) + off) = __float2half_rn(b);
 }
@@ -553,7 +575,8 @@ int sm_count_g() {
 }
 
 int kx_of(int d) { return 3 * (d + 2) <= 64 ? 64 : 128; }
-int tm_of(int t) { return (t + 15) / 16 * 16; }
+int kx3_of(int d) { return (6 * (d + 2) + 15) / 16 * 16; }   // the product's three-part form
+int tm_of(int t) { return (3 * t + 15) / 16 * 16; }   // three hi / lo segments of t
 int nr_of(int d) { return (4 + 4 * d + 15) / 16 * 16; }
 int ntiles_of(int64_t n) { return (int)cdiv(n, BM); }
 
@@ -631,6 +654,9 @@ gp_status contract_tc(const Prob& pb, const void* Xs, const TcBufs& tb, const Tc
   GradArgs a;
   a.xa = static_cast<const __nv_bfloat16*>(tb.xpack);
   a.xb = a.xa + (size_t)nt * BM * kx;
+  const int kx3 = kx3_of(pb.d);
+  a.xa3 = a.xb + (size_t)nt * BN * kx;        // layout of tc_prepare_inputs
+  a.xb3 = a.xa3 + (size_t)nt * BM * kx3;
   a.ma = ma;
   a.mb = mb;
   a.xr = xr;
@@ -643,17 +669,27 @@ gp_status contract_tc(const Prob& pb, const void* Xs, const TcBufs& tb, const Tc
   a.tiles_per_chunk = (int)cdiv(nt, nch);
   a.nchunks = (int)cdiv(nt, a.tiles_per_chunk);
   a.kx = kx;
+  a.kx3 = kx3;
   a.tm = tm;
   a.nr = nr;
   a.d = pb.d;
   a.kind = pb.kind;
-  a.ns = stages_of(kx, tm, nr);
+  // shared memory for the wider of the two exponent forms when it fits (the split flag
+  // is read on the device); otherwise split mode keeps the two-part exponent here
+  const int kwide = std::max(kx, kx3);
+  int kxs = kwide;
+  a.ns = stages_of(kwide, tm, nr);
+  if (a.ns < 2) {
+    kxs = kx;
+    a.ns = stages_of(kx, tm, nr);
+  }
+  a.kx3_ok = kx3 <= kxs ? 1 : 0;
   a.err = tb.err;
   if (a.ns < 2) {
     set_error("gradient contraction: shape does not fit shared memory");
     return GP_ERR_INVALID_ARG;
   }
-  const size_t sm = smem_of(kx, tm, nr, a.ns);
+  const size_t sm = smem_of(kxs, tm, nr, a.ns);
   static bool attr_set = false;
   if (!attr_set) {
     GP_CUDA_TRY(cudaFuncSetAttribute(grad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -9,7 +9,10 @@
 //          Matern: c = 1     ->  r = sqrt(-2 S), k / s = poly(r) e^{-a r}.
 //          Each operand is split into BF16 hi + lo parts and the product is formed as
 //          hi.hi + hi.lo + lo.hi, which keeps ~16 significant bits in S despite the
-//          cancellation between the norms and the dot product.
+//          cancellation between the norms and the dot product.  Split mode (below) uses
+//          a three-part split hi + mid + lo and the six products of total order <= 2
+//          (~24 bits): on inputs with large norms (|x|^2 ~ 30) the 16-bit form
+//          perturbs K by |dK|_2 ~ 1e-6 n, which exceeds sigma^2 = 0.1 at n = 5e5.
 //   epilogue  P = k(S) / s in [0, 1], FP32 in registers, rounded to FP16 (11
 //          significant bits) and written back over the same TMEM columns;
 //          tcgen05.ld / tcgen05.st, one thread per row.
@@ -77,11 +80,14 @@ constexpr int kPBuf = 2;       // FP16 P buffers in TMEM (64 columns each; split
 constexpr int kEpiWarps = 16;
 
 struct TcArgs {
-  const __nv_bfloat16* xa;   // ntiles tiles of BM x kx (A form)
+  const __nv_bfloat16* xa;   // ntiles tiles of BM x kx (A form, two-part split)
   const __nv_bfloat16* xb;   // ntiles tiles of BN x kx (B form)
+  const __nv_bfloat16* xa3;  // the same with the three-part split (split mode), kx3 wide
+  const __nv_bfloat16* xb3;
   const __half* vp;          // ntiles tiles of 2 tp x BN (FP16 hi and lo parts)
   float* part;               // nchunks x tp x npad
-  int n, npad, ntiles, nchunks, tiles_per_chunk, kx, tp, t, kind, D;
+  int n, npad, ntiles, nchunks, tiles_per_chunk, kx, kx3, tp, t, kind, D;
+  int kx3_ok;                // shared memory fits the three-part operands
   int nsb, nsv;              // shared-memory stages of the B and V rings (2 .. 4)
   const int* gate;
   int* err;                  // err[0] = status, err[1] = where a wait gave up,
@@ -141,8 +147,14 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   if (g.gate && *g.gate == 0) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kx = g.kx, tp = g.tp, nsb = g.nsb, nsv = g.nsv;
   const bool split = g.err[2] != 0;
+  // split mode: the three-part exponent operands, when the launch's shared memory was
+  // sized for them (always, unless the host knew the flag was off or the shape is too
+  // wide for them)
+  const bool wide = split && g.kx3_ok;
+  const int kx = wide ? g.kx3 : g.kx, tp = g.tp, nsb = g.nsb, nsv = g.nsv;
+  const __nv_bfloat16* xa = wide ? g.xa3 : g.xa;
+  const __nv_bfloat16* xb = wide ? g.xb3 : g.xb;
   const uint32_t npb = split ? 1u : (uint32_t)kPBuf;   // P buffers in the ring
   const uint32_t a_bytes = BM * kx * 2, b_bytes = BN * kx * 2;
   const uint32_t v_bytes = 2u * tp * BN * 2;   // FP16 hi and lo parts of V
@@ -201,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
       const int ns = is_b ? nsb : nsv;
       const uint32_t bytes = is_b ? b_bytes : v_bytes;
       unsigned char* sbase = is_b ? sB : sV;
-      const unsigned char* gsrc = is_b ? reinterpret_cast<const unsigned char*>(g.xb)
+      const unsigned char* gsrc = is_b ? reinterpret_cast<const unsigned char*>(xb)
                                        : reinterpret_cast<const unsigned char*>(g.vp);
       unsigned long long* fullr = is_b ? bars->fullB : bars->fullV;
       unsigned long long* emptyr = is_b ? bars->emptyB : bars->emptyV;
@@ -220,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
           first = false;
           mbar_expect_tx(smem_u32(&bars->a_full), a_bytes);
           bulk_g2s(smem_u32(sA),
-                   reinterpret_cast<const unsigned char*>(g.xa) + (size_t)rt * a_bytes, a_bytes,
+                   reinterpret_cast<const unsigned char*>(xa) + (size_t)rt * a_bytes, a_bytes,
                    smem_u32(&bars->a_full));
           ++a_arms;
         }
@@ -287,12 +299,8 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         tc_fence_after();
         const uint64_t db = dB0 + st * b_step;
         const uint32_t ts = tmem + buf * 128;
-        for (int k0 = 0; k0 < nk1; k0 += 4) {   // kx is 64 or 128
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            mma_ss(ts, dA + (uint64_t)(k0 + q) * 16, db + (uint64_t)(k0 + q) * 16, id1,
-                   (k0 + q) > 0 ? 1u : 0u);
-        }
+        for (int q = 0; q < nk1; ++q)   // kx / 16 K steps (4 .. 13)
+          mma_ss(ts, dA + (uint64_t)q * 16, db + (uint64_t)q * 16, id1, q > 0 ? 1u : 0u);
         mma_commit(smem_u32(&bars->s_full[buf]));
         mma_commit(smem_u32(&bars->emptyB[st]));
         if (jj == nt - 1) mma_commit(smem_u32(&bars->a_free));
@@ -488,17 +496,35 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
 }
 
 // ---- packing kernels ------------------------------------------------------------------
-// Augmented exponent operands, hi/lo split, in the canonical tile layout.
-// A_i = [c x, 1, -c |x|^2/2] ; B_j = [x, -c |x|^2/2, 1]; A' = [A_hi, A_hi, A_lo],
-// B' = [B_hi, B_lo, B_hi], zero padded to kx.
-__global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __restrict__ Xs,
-                              int kind, const double* __restrict__ theta, int D,
+// Augmented exponent operands in the canonical tile layout:
+// A_i = [c x, 1, -c |x|^2/2] ; B_j = [x, -c |x|^2/2, 1], each entry split into BF16
+// parts v = p0 + p1 (+ p2), p_m = bf16(v - p_0 - .. - p_{m-1}).  Segments of d + 2
+// columns pair the parts whose products are kept:
+//   two parts:   (p0, p0), (p0, p1), (p1, p0)                              (~16 bits)
+//   three parts: (p0, p0), (p0, p1), (p1, p0), (p0, p2), (p1, p1), (p2, p0)  (~24 bits)
+// so that A' . B' = sum of the kept products; zero padded to kx.
+__device__ __forceinline__ void bf16_parts(double v, float (&pt)[3]) {
+  const float p0 = __bfloat162float(__float2bfloat16_rn((float)v));
+  const float p1 = __bfloat162float(__float2bfloat16_rn((float)(v - (double)p0)));
+  const float p2 =
+      __bfloat162float(__float2bfloat16_rn((float)(v - (double)p0 - (double)p1)));
+  pt[0] = p0;
+  pt[1] = p1;
+  pt[2] = p2;
+}
+
+__global__ void pack_x_kernel(int n, int ntiles, int d, int kx, int parts,
+                              const float* __restrict__ Xs, int kind,
                               __nv_bfloat16* __restrict__ xa, __nv_bfloat16* __restrict__ xb,
                               float* __restrict__ norms) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntiles * BM) return;
   const double c = (kind == GP_RBF) ? 1.4426950408889634 : 1.0;
   const int L = d + 2;
+  // part of A (first) and of B (second) in each segment
+  constexpr int kSegA[6] = {0, 0, 1, 0, 1, 2};
+  constexpr int kSegB[6] = {0, 1, 0, 2, 1, 0};
+  const int nseg = parts == 3 ? 6 : 3;
   double av[kMaxD + 2], bv[kMaxD + 2];
   double nrm = 0.0;
   const bool valid = i < n;
@@ -512,20 +538,19 @@ __global__ void pack_x_kernel(int n, int ntiles, int d, int kx, const float* __r
   av[d + 1] = valid ? -0.5 * c * nrm : 0.0;
   bv[d] = valid ? -0.5 * c * nrm : 0.0;
   bv[d + 1] = valid ? 1.0 : 0.0;
-  if (valid) norms[i] = (float)nrm;
+  if (valid && norms) norms[i] = (float)nrm;
   const int tile = i / BM, r = i % BM;
   unsigned char* ta = reinterpret_cast<unsigned char*>(xa) + (size_t)tile * BM * kx * 2;
   unsigned char* tb = reinterpret_cast<unsigned char*>(xb) + (size_t)tile * BN * kx * 2;
   for (int k = 0; k < kx; ++k) {
     float va = 0.f, vb = 0.f;
-    int seg = k / L, q = k % L;
-    if (seg < 3) {
-      double x = av[q], y = bv[q];
-      float xh = __bfloat162float(__float2bfloat16_rn((float)x));
-      float yh = __bfloat162float(__float2bfloat16_rn((float)y));
-      float xl = (float)(x - (double)xh), yl = (float)(y - (double)yh);
-      va = (seg == 2) ? xl : xh;        // [hi, hi, lo]
-      vb = (seg == 1) ? yl : yh;        // [hi, lo, hi]
+    const int seg = k / L, q = k % L;
+    if (seg < nseg) {
+      float pa[3], pb[3];
+      bf16_parts(av[q], pa);
+      bf16_parts(bv[q], pb);
+      va = pa[kSegA[seg]];
+      vb = pb[kSegB[seg]];
     }
     *reinterpret_cast<__nv_bfloat16*>(ta + tile_off(r, k, kx)) = __float2bfloat16_rn(va);
     *reinterpret_cast<__nv_bfloat16*>(tb + tile_off(r, k, kx)) = __float2bfloat16_rn(vb);
@@ -628,6 +653,7 @@ int sm_count() {
 }
 
 int kx_for(int d) { return 3 * (d + 2) <= 64 ? 64 : 128; }
+int kx3_for(int d) { return (6 * (d + 2) + 15) / 16 * 16; }   // three-part form
 int tp_for(int t) { return (t + 7) / 8 * 8; }
 int ntiles_for(int64_t n) { return (int)cdiv(n, BM); }
 int nchunks_for(int ntiles) {
@@ -687,7 +713,8 @@ void stages_for(int kx, int tp, int* nsb, int* nsv) {
 
 size_t tc_xpack_bytes(int64_t n, int d, int prec) {
   (void)prec;
-  return (size_t)ntiles_for(n) * BM * kx_for(d) * 2 * 2;   // A and B forms
+  // A and B forms of the two-part split, then of the three-part split
+  return (size_t)ntiles_for(n) * BM * (kx_for(d) + kx3_for(d)) * 2 * 2;
 }
 size_t tc_vpack_bytes(int64_t n, int t, int prec) {
   (void)prec;
@@ -702,27 +729,45 @@ bool tc_supported(const Prob& pb, int t) {
 }
 
 gp_status tc_prepare_inputs(const Prob& pb, const void* Xs, const TcBufs& tb, cudaStream_t st) {
-  const int nt = ntiles_for(pb.n), kx = kx_for(pb.d);
+  const int nt = ntiles_for(pb.n), kx = kx_for(pb.d), kx3 = kx3_for(pb.d);
   __nv_bfloat16* xa = static_cast<__nv_bfloat16*>(tb.xpack);
   __nv_bfloat16* xb = xa + (size_t)nt * BM * kx;
-  pack_x_kernel<<<(unsigned)cdiv((int64_t)nt * BM, 128), 128, 0, st>>>(
-      (int)pb.n, nt, pb.d, kx, static_cast<const float*>(Xs), pb.kind, pb.theta, pb.D, xa, xb,
-      tb.norms);
+  __nv_bfloat16* xa3 = xb + (size_t)nt * BN * kx;
+  __nv_bfloat16* xb3 = xa3 + (size_t)nt * BM * kx3;
+  const unsigned blocks = (unsigned)cdiv((int64_t)nt * BM, 128);
+  pack_x_kernel<<<blocks, 128, 0, st>>>((int)pb.n, nt, pb.d, kx, 2,
+                                        static_cast<const float*>(Xs), pb.kind, xa, xb,
+                                        tb.norms);
+  GP_LAUNCH_CHECK();
+  pack_x_kernel<<<blocks, 128, 0, st>>>((int)pb.n, nt, pb.d, kx3, 3,
+                                        static_cast<const float*>(Xs), pb.kind, xa3, xb3,
+                                        nullptr);
   GP_LAUNCH_CHECK();
   return GP_OK;
 }
 
 gp_status kmvm_tc(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t, float* W,
-                  int64_t ldw, const int* gate, cudaStream_t st) {
-  return kmvm_tc_debug(pb, tb, V, ldv, t, W, ldw, gate, nullptr, st);
+                  int64_t ldw, const int* gate, int mode, cudaStream_t st) {
+  return kmvm_tc_debug(pb, tb, V, ldv, t, W, ldw, gate, nullptr, mode, st);
 }
 
 namespace {
+// mode: 0 = fast (the split flag is known to be off), 1 = split (known on), 2 = read
+// on the device (shared memory sized for the wider split-mode operands).
 gp_status kmvm_tc_cfg(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
                       float* W, int64_t ldw, const int* gate, float* dbg, const TcConfig* cfg,
-                      cudaStream_t st) {
+                      int mode, cudaStream_t st) {
   const int n = (int)pb.n;
-  const int nt = ntiles_for(pb.n), kx = kx_for(pb.d), tp = tp_for(t);
+  const int nt = ntiles_for(pb.n), kx = kx_for(pb.d), kx3 = kx3_for(pb.d), tp = tp_for(t);
+  // Operand width the shared memory is sized for.  Invariant: the kernel never uses
+  // a wider form than this (it takes the three-part form only when kx3 <= kxs, and
+  // kxs >= kx always), whatever the split flag holds at launch.  kx3 can be narrower
+  // than kx (small d: kx is padded to 64), so the width is the larger of the two
+  // whenever the flag may be on; when the three-part tiles do not fit at all, split
+  // mode keeps the two-part exponent.
+  const int kwide = std::max(kx, kx3);
+  const bool fit3 = smem_bytes(kwide, tp, 2, 2) <= kSmemCap;
+  const int kxs = (mode != 0 && fit3) ? kwide : kx;
   const int nch = cfg ? std::min(cfg->nchunks, max_chunks_for(nt)) : nchunks_for(nt);
   const int npad = nt * BM;
   __nv_bfloat16* xa = static_cast<__nv_bfloat16*>(tb.xpack);
@@ -739,6 +784,8 @@ gp_status kmvm_tc_cfg(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
   TcArgs a;
   a.xa = xa;
   a.xb = xb;
+  a.xa3 = xb + (size_t)nt * BN * kx;
+  a.xb3 = a.xa3 + (size_t)nt * BM * kx3;
   a.vp = vp;
   a.part = tb.part;
   a.n = n;
@@ -747,12 +794,14 @@ gp_status kmvm_tc_cfg(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
   a.nchunks = nch;
   a.tiles_per_chunk = (int)cdiv(nt, nch);
   a.kx = kx;
+  a.kx3 = kx3;
+  a.kx3_ok = kx3 <= kxs ? 1 : 0;
   a.tp = tp;
   a.t = t;
   a.kind = pb.kind;
   a.D = pb.D;
-  stages_for(kx, tp, &a.nsb, &a.nsv);
-  if (cfg && cfg->nsb >= 2 && cfg->nsv >= 2 && smem_bytes(kx, tp, cfg->nsb, cfg->nsv) <= kSmemCap) {
+  stages_for(kxs, tp, &a.nsb, &a.nsv);
+  if (cfg && cfg->nsb >= 2 && cfg->nsv >= 2 && smem_bytes(kxs, tp, cfg->nsb, cfg->nsv) <= kSmemCap) {
     a.nsb = cfg->nsb;
     a.nsv = cfg->nsv;
   }
@@ -761,7 +810,7 @@ gp_status kmvm_tc_cfg(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
   a.dbg = dbg;
   // the chunk count must not leave an empty chunk
   a.nchunks = (int)cdiv(nt, a.tiles_per_chunk);
-  const size_t sm = smem_bytes(kx, tp, a.nsb, a.nsv);
+  const size_t sm = smem_bytes(kxs, tp, a.nsb, a.nsv);
   static bool attr_set = false;
   if (!attr_set) {
     GP_CUDA_TRY(cudaFuncSetAttribute(kmvm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -780,12 +829,13 @@ gp_status kmvm_tc_cfg(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
 }  // namespace
 
 gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
-                        float* W, int64_t ldw, const int* gate, float* dbg, cudaStream_t st) {
+                        float* W, int64_t ldw, const int* gate, float* dbg, int mode,
+                        cudaStream_t st) {
   // the split flag is on the device; the tuned table is keyed on fast mode, which is
   // what the tuner times (split mode has the same tiling and ring structure)
   TcConfig c;
   const bool tuned = tune_lookup(tune_key(kx_for(pb.d), tp_for(t), pb.kind, 0, ntiles_for(pb.n)), &c);
-  return kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, gate, dbg, tuned ? &c : nullptr, st);
+  return kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, gate, dbg, tuned ? &c : nullptr, mode, st);
 }
 
 // Times the candidate configurations for this problem shape (one warm-up and three
@@ -809,11 +859,11 @@ gp_status tc_autotune(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
   TcConfig bc;
   gp_status rs = GP_OK;
   for (const TcConfig& c : cands) {
-    rs = kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &c, st);
+    rs = kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &c, 0, st);
     if (rs != GP_OK) break;
     cudaEventRecord(e0, st);
     for (int r = 0; r < 3 && rs == GP_OK; ++r)
-      rs = kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &c, st);
+      rs = kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &c, 0, st);
     cudaEventRecord(e1, st);
     if (rs != GP_OK) break;
     float ms = 0.f;
@@ -840,7 +890,7 @@ gp_status tc_autotune(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
     best_out[3] = (int)cands.size();
   }
   // W from the chosen configuration
-  return kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &bc, st);
+  return kmvm_tc_cfg(pb, tb, V, ldv, t, W, ldw, nullptr, nullptr, &bc, 0, st);
 }
 
 // The configuration the product uses for this shape: {nchunks, nsb, nsv, tuned}.

@@ -38,7 +38,7 @@ gp_status contract_simt(const Prob& pb, const void* Xs, const void* A, int64_t l
 
 // ---- tensor-core kernel products (kmvm_tc.cu) -----------------------------------
 struct TcBufs {
-  void* xpack;       // packed hi/lo operand tiles of the scaled inputs
+  void* xpack;       // packed exponent operand tiles: two-part (A, B), three-part (A, B)
   float* norms;      // n
   void* vpack;       // packed right-hand-side tiles
   float* vscale;     // kTcVscaleElems: column scales of V, their inverses, partial maxima
@@ -53,8 +53,10 @@ size_t tc_vpack_bytes(int64_t n, int t, int prec);
 size_t tc_part_elems(int64_t n, int t);
 bool tc_supported(const Prob& pb, int t);
 gp_status tc_prepare_inputs(const Prob& pb, const void* Xs, const TcBufs& tb, cudaStream_t st);
+// mode: 0 fast, 1 split (three-part exponent operands, FP16 hi + lo k(r)/s), 2 chosen
+// on the device by the split flag (err[2]) at launch.
 gp_status kmvm_tc(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
-                  float* W, int64_t ldw, const int* gate, cudaStream_t st);
+                  float* W, int64_t ldw, const int* gate, int mode, cudaStream_t st);
 // Same, and (dbg != null) the exponent tile S of the first tile pair -> dbg (128 x 128).
 // Autotuner of the TC launch configuration (column chunks, ring depths) for this
 // shape; best_out (may be null) = {nchunks, nsb, nsv, candidates timed}.
@@ -62,7 +64,8 @@ gp_status tc_autotune(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
                       float* W, int64_t ldw, cudaStream_t st, int* best_out);
 void tc_config(const Prob& pb, int t, int* out4);
 gp_status kmvm_tc_debug(const Prob& pb, const TcBufs& tb, const float* V, int64_t ldv, int t,
-                        float* W, int64_t ldw, const int* gate, float* dbg, cudaStream_t st);
+                        float* W, int64_t ldw, const int* gate, float* dbg, int mode,
+                        cudaStream_t st);
 
 // ---- tensor-core gradient contraction (grad_tc.cu) ---------------------------------
 // The contraction of contract_simt (lengthscale and output-scale entries) for the

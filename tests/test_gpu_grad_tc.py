@@ -9,9 +9,9 @@ is identical in both (the contraction runs after it), so:
 * the two MLLs agree bit for bit, and the difference of their contraction outputs
   isolates the tensor-core contraction's own arithmetic.  It evaluates k(r) from the
   product's exponent tile (BF16 hi / lo operands, |dS| ~ 2e-5 on these inputs), where
-  the CUDA-core form uses FP32 differences; then FP16 M operands with power-of-two
-  column scales, H as FP16 hi + lo, FP16 hi / lo coordinates, FP32 accumulation and an
-  FP64 row combination.  A CPU emulation of every one of those rounding steps puts the
+  the CUDA-core form uses FP32 differences; then FP16 hi / lo M operands with
+  power-of-two column scales, H as FP16 hi + lo, FP16 hi / lo coordinates, FP32
+  accumulation and an FP64 row combination.  A CPU emulation of every one of those rounding steps puts the
   gradient entries within 5.7e-4 of the exact contraction, relative to
   1/2 (|quad_p| + |trace_p|) (the output-scale entry of the isotropic Matern-3/2
   problem; 4.8e-4 of it from the exponent tile alone), and within 1.2e-4 without the
@@ -69,6 +69,9 @@ PROBLEMS = {
     # the n = 5e5 Matern-3/2 ARD workload's shape (Gaussian-mixture inputs, d = 10, t = 17)
     "matern32_ard_d10": lambda: _with(workloads.subsample(workloads.c4_matern32_5e5(n=20000),
                                                           2000), k=100),
+    # the n = 5e5 Matern-3/2 workload's own settings (k = 500, l = 16, tol 1e-2)
+    "matern32_ard_c4_k500": lambda: workloads.subsample(workloads.c4_matern32_5e5(n=20000),
+                                                        2000),
     # the Matern-5/2 ARD workload's shape (d = 8, t = 51, tol 1e-3)
     "matern52_ard_d8": lambda: _with(workloads.subsample(workloads.c2_matern52_ard(n=20000),
                                                          1500), n_probes=24),
