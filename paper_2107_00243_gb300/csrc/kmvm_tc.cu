@@ -622,7 +622,8 @@ __global__ void pack_v_kernel(int n, int ntiles, int t, int tp, const float* __r
   *reinterpret_cast<__half*>(tv + part + tile_off(c, k, BN)) = __float2half_rn(v - __half2float(hi));
 }
 
-// W = s / scale_c * (sum over chunks) + sigma^2 V (NaN on a device-side abort).
+// W = s / scale_c * (sum over chunks) + sigma^2 V (NaN on a device-side abort); the
+// chunk partials are added in FP64.
 __global__ void tc_reduce_kernel(int n, int npad, int t, int tp, int nchunks,
                                  const float* __restrict__ part,
                                  const float* __restrict__ V, int64_t ldv,
@@ -633,12 +634,12 @@ __global__ void tc_reduce_kernel(int n, int npad, int t, int tp, int nchunks,
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)n * t) return;
   const int c = (int)(e / n), i = (int)(e % n);
-  float acc = 0.f;
-  for (int ch = 0; ch < nchunks; ++ch) acc += part[((size_t)ch * tp + c) * npad + i];
-  acc *= (float)theta[D] * vscale[kMaxT64 + c];
-  acc = fmaf((float)theta[D + 1], V[i + (int64_t)c * ldv], acc);
-  if (*err) acc = __int_as_float(0x7fc00000);
-  W[i + (int64_t)c * ldw] = acc;
+  double acc = 0.0;
+  for (int ch = 0; ch < nchunks; ++ch) acc += (double)part[((size_t)ch * tp + c) * npad + i];
+  acc = acc * theta[D] * (double)vscale[kMaxT64 + c] + theta[D + 1] * (double)V[i + (int64_t)c * ldv];
+  float w = (float)acc;
+  if (*err) w = __int_as_float(0x7fc00000);
+  W[i + (int64_t)c * ldw] = w;
 }
 
 int sm_count() {
@@ -656,10 +657,21 @@ int kx_for(int d) { return 3 * (d + 2) <= 64 ? 64 : 128; }
 int kx3_for(int d) { return (6 * (d + 2) + 15) / 16 * 16; }   // three-part form
 int tp_for(int t) { return (t + 7) / 8 * 8; }
 int ntiles_for(int64_t n) { return (int)cdiv(n, BM); }
+// Large problems split every row's sum into chunks of at most kChunkTiles column tiles:
+// each output then accumulates in FP32 (TMEM) over at most 8 kChunkTiles MMA steps and
+// the chunk partials are added in FP64.  One FP32 accumulator over all 3,907 column
+// tiles of n = 5e5 (31k MMA steps) leaves rounding of ~1e-5 (|K||v|)_i, which in the
+// small-eigenvalue directions of an ill-conditioned K (lambda_max / sigma^2 ~ 1e5) is of
+// the order of sigma^2 itself, and CG on probe vectors diverged there.
+constexpr int kChunkTiles = 64;
+constexpr int kLongRow = 1024;   // rows of more column tiles than this are chunked
+int min_chunks_for(int ntiles) {
+  return ntiles > kLongRow ? (int)cdiv(ntiles, kChunkTiles) : 1;
+}
 int nchunks_for(int ntiles) {
   int want = (int)cdiv(8LL * 152, ntiles);
   int maxc = std::max(1, ntiles / 16);
-  return std::max(1, std::min(want, maxc));
+  return std::max(min_chunks_for(ntiles), std::max(1, std::min(want, maxc)));
 }
 // Largest column-chunk count the autotuner may pick (the partial-sum buffer is sized
 // for it): chunks of at least 4 tiles, and no more than ~16 work units per SM.
@@ -768,7 +780,8 @@ gp_status kmvm_tc_cfg(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
   const int kwide = std::max(kx, kx3);
   const bool fit3 = smem_bytes(kwide, tp, 2, 2) <= kSmemCap;
   const int kxs = (mode != 0 && fit3) ? kwide : kx;
-  const int nch = cfg ? std::min(cfg->nchunks, max_chunks_for(nt)) : nchunks_for(nt);
+  const int nch = cfg ? std::max(min_chunks_for(nt), std::min(cfg->nchunks, max_chunks_for(nt)))
+                      : nchunks_for(nt);
   const int npad = nt * BM;
   __nv_bfloat16* xa = static_cast<__nv_bfloat16*>(tb.xpack);
   __nv_bfloat16* xb = xa + (size_t)nt * BM * kx;
