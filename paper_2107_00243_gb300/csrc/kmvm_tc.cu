@@ -622,8 +622,10 @@ __global__ void pack_v_kernel(int n, int ntiles, int t, int tp, const float* __r
   *reinterpret_cast<__half*>(tv + part + tile_off(c, k, BN)) = __float2half_rn(v - __half2float(hi));
 }
 
-// W = s / scale_c * (sum over chunks) + sigma^2 V (NaN on a device-side abort); the
-// chunk partials are added in FP64.
+// W = s / scale_c * (sum over chunks) + sigma^2 V (NaN on a device-side abort).  The
+// chunk partials are added with Neumaier's compensated summation in FP32 (FP64
+// arithmetic runs at 1/64 of the FP32 rate on this part, which made this pass a few
+// percent of every product).
 __global__ void tc_reduce_kernel(int n, int npad, int t, int tp, int nchunks,
                                  const float* __restrict__ part,
                                  const float* __restrict__ V, int64_t ldv,
@@ -634,10 +636,16 @@ __global__ void tc_reduce_kernel(int n, int npad, int t, int tp, int nchunks,
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)n * t) return;
   const int c = (int)(e / n), i = (int)(e % n);
-  double acc = 0.0;
-  for (int ch = 0; ch < nchunks; ++ch) acc += (double)part[((size_t)ch * tp + c) * npad + i];
-  acc = acc * theta[D] * (double)vscale[kMaxT64 + c] + theta[D + 1] * (double)V[i + (int64_t)c * ldv];
-  float w = (float)acc;
+  float sum = 0.f, comp = 0.f;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const float x = part[((size_t)ch * tp + c) * npad + i];
+    const float tsum = __fadd_rn(sum, x);
+    comp = __fadd_rn(comp, fabsf(sum) >= fabsf(x) ? __fadd_rn(__fadd_rn(sum, -tsum), x)
+                                                   : __fadd_rn(__fadd_rn(x, -tsum), sum));
+    sum = tsum;
+  }
+  const float acc = __fadd_rn(sum, comp) * ((float)theta[D] * vscale[kMaxT64 + c]);
+  float w = fmaf((float)theta[D + 1], V[i + (int64_t)c * ldv], acc);
   if (*err) w = __int_as_float(0x7fc00000);
   W[i + (int64_t)c * ldw] = w;
 }
@@ -659,10 +667,11 @@ int tp_for(int t) { return (t + 7) / 8 * 8; }
 int ntiles_for(int64_t n) { return (int)cdiv(n, BM); }
 // Large problems split every row's sum into chunks of at most kChunkTiles column tiles:
 // each output then accumulates in FP32 (TMEM) over at most 8 kChunkTiles MMA steps and
-// the chunk partials are added in FP64.  One FP32 accumulator over all 3,907 column
+// the chunk partials are added with compensation.  One FP32 accumulator over all 3,907 column
 // tiles of n = 5e5 (31k MMA steps) leaves rounding of ~1e-5 (|K||v|)_i, which in the
 // small-eigenvalue directions of an ill-conditioned K (lambda_max / sigma^2 ~ 1e5) is of
-// the order of sigma^2 itself, and CG on probe vectors diverged there.
+// the order of sigma^2 itself, and CG on probe vectors diverged there.  (The partials
+// are summed with compensation in tc_reduce_kernel.)
 constexpr int kChunkTiles = 64;
 constexpr int kLongRow = 1024;   // rows of more column tiles than this are chunked
 int min_chunks_for(int ntiles) {
