@@ -279,11 +279,10 @@ const char* gp_last_error_message(void);
 
 /* The kernel-matrix product of gp_kernel_mvm, W = (K + sigma^2 I) V, for callers that
  * cannot allocate device memory.  Such callers include:
- *   - code running where cudaMalloc is off limits, e.g. inside someone else's
- *     graph-capture region;
- *   - real-time loops with a fixed memory budget;
+ *   - real-time loops with a fixed memory budget, where a device allocation (or the
+ *     synchronisation it can cause) is not allowed once the loop runs;
  *   - host frameworks that own the allocator and hand the library only its input and
- *     output buffers.
+ *     output buffers, with no room for a workspace of the library's own.
  * The paper has no counterpart: this repackages gp_kernel_mvm without a workspace.
  *
  * Scratch.  One static device array of 16 MiB + 80 KiB inside this library.  Every

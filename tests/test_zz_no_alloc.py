@@ -1,18 +1,20 @@
 """gp_kernel_mvm_noalloc: the kernel-matrix product for callers that cannot allocate
-device memory (code inside someone else's graph capture, real-time loops with a fixed
-budget, frameworks that own the allocator).  Its scratch is a static device array in
-the library, reused by every call.
+device memory (real-time loops with a fixed memory budget, frameworks that own the
+allocator and hand the library only its inputs and outputs).  Its scratch is a static
+device array in the library, reused by every call.
 
 Checked through the C ABI against gp_kernel_mvm (which uses a caller workspace) on
 two calls in a row, the second smaller than the first so that contents left in the
 shared array by the first call cannot leak into the second; the bound is the kernel
-product's parity tolerance (2e-5 normwise in FP32, 1e-11 in FP64).  Sizes beyond the
-array are rejected before anything runs.  Collected last on purpose.
+product's parity tolerance (2e-5 normwise in FP32, 1e-11 in FP64), and against the
+FP64 oracle's product at the same tolerance.  Sizes beyond the array are rejected
+before anything runs.  Collected last on purpose.
 """
 import numpy as np
 import pytest
 import torch
 
+from oracle import kernels
 from paper_2107_00243_gb300 import gp, workloads
 
 pytestmark = pytest.mark.gpu
@@ -44,6 +46,9 @@ def test_noalloc_matches_kernel_mvm_on_two_calls(prec):
         torch.cuda.synchronize()
         assert got.shape == (n, t)
         assert _rel(got, ref) <= TOL[prec], _rel(got, ref)
+        exact = torch.from_numpy(
+            kernels.KernelOperator(kind, p.X, p.theta, True).matvec(V.numpy()))
+        assert _rel(got.cpu().double(), exact) <= TOL[prec], _rel(got.cpu().double(), exact)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
