@@ -11,6 +11,9 @@ to k(x, x) (the paper writes o^2 = k(0) in Prop. "Cholesky approximation quality
     RBF      k = s exp(-r^2 / 2)
     Matern32 k = s (1 + sqrt(3) r) exp(-sqrt(3) r)
     Matern52 k = s (1 + sqrt(5) r + 5 r^2 / 3) exp(-sqrt(5) r)
+    RatQuad  k = s (1 + r^2 / (2 alpha))^-alpha with alpha = 1, i.e. s / (1 + r^2 / 2)
+             (Rasmussen & Williams 2006, eq. 4.19; the paper's RatQuad kernel, Tab. S1,
+             does not state alpha: it is read as 1 and held fixed, not a hyperparameter)
 
 Hyperparameters are theta = (l_1..l_D, s, sigma^2) with D = d (ARD) or 1
 (isotropic).  Derivatives are taken with respect to these raw values.
@@ -22,6 +25,7 @@ d k / d l_j = -2 (dk/d r^2) (dx_j)^2 / l_j^3.  ``neg2_dk_dr2`` below is the fact
     RBF      -2 dk/dr^2 = s exp(-r^2/2)
     Matern32 -2 dk/dr^2 = 3 s exp(-sqrt(3) r)
     Matern52 -2 dk/dr^2 = (5/3) s (1 + sqrt(5) r) exp(-sqrt(5) r)
+    RatQuad  -2 dk/dr^2 = s (1 + r^2/2)^-2
 
 (For Matern: dk/dr = -s a^2 r exp(-a r) with a = sqrt(3), resp.
 -s (a^2/3) r (1 + a r) exp(-a r) with a = sqrt(5); dividing by dr^2/dr = 2 r gives
@@ -32,7 +36,8 @@ import numpy as np
 RBF = 0
 MATERN32 = 3
 MATERN52 = 5
-KINDS = (RBF, MATERN32, MATERN52)
+RATQUAD = 7
+KINDS = (RBF, MATERN32, MATERN52, RATQUAD)
 
 
 def n_lengthscales(d, ard):
@@ -57,6 +62,8 @@ def k_of_r2(kind, r2, s):
     r2 = np.maximum(r2, 0.0)
     if kind == RBF:
         return s * np.exp(-0.5 * r2)
+    if kind == RATQUAD:
+        return s / (1.0 + 0.5 * r2)
     r = np.sqrt(r2)
     if kind == MATERN32:
         a = np.sqrt(3.0)
@@ -72,6 +79,8 @@ def neg2_dk_dr2(kind, r2, s):
     r2 = np.maximum(r2, 0.0)
     if kind == RBF:
         return s * np.exp(-0.5 * r2)
+    if kind == RATQUAD:
+        return s / (1.0 + 0.5 * r2) ** 2
     r = np.sqrt(r2)
     if kind == MATERN32:
         a = np.sqrt(3.0)

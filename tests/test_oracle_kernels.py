@@ -4,10 +4,15 @@
   Bessel function K_nu (Rasmussen & Williams 2006, eq. 4.14), evaluated by scipy.
 * RBF is the nu -> infinity limit of Matern, and an ARD RBF factorises over
   dimensions.
+* The rational quadratic kernel is a scale mixture of RBF kernels:
+  (1 + r^2/(2 alpha))^-alpha = int_0^inf exp(-tau r^2 / 2) Gamma(tau; alpha, rate alpha) dtau
+  (Rasmussen & Williams 2006, eq. 4.20), evaluated by numerical quadrature over the
+  oracle's own RBF; it also approaches the RBF as alpha grows (checked on the general form).
 * Every derivative equals a central finite difference of the kernel value.
 """
 import numpy as np
 import pytest
+from scipy import integrate
 from scipy.special import gammaln, kve
 
 from oracle import kernels
@@ -102,3 +107,26 @@ def test_operator_matches_dense():
     dK = kernels.dkhat_dense(kernels.MATERN52, X, theta, True)
     for got, ref in zip(op.grad_matvec(V), dK):
         np.testing.assert_allclose(got, ref @ V, rtol=1e-12, atol=1e-12)
+
+
+def test_ratquad_is_gamma_mixture_of_rbf():
+    alpha = 1.0
+    s_out = 1.4
+    for r in (0.0, 0.3, 1.0, 2.5, 6.0):
+        def integrand(tau):
+            gamma_pdf = np.exp(alpha * np.log(alpha) - gammaln(alpha)
+                               + (alpha - 1.0) * np.log(tau) - alpha * tau)
+            return float(kernels.k_of_r2(kernels.RBF, tau * r * r, s_out)) * gamma_pdf
+        val, err = integrate.quad(integrand, 0.0, np.inf, epsabs=1e-14, epsrel=1e-12)
+        got = float(kernels.k_of_r2(kernels.RATQUAD, np.array(r * r), s_out))
+        assert abs(got - val) <= 1e-10 * s_out, (r, got, val)
+
+
+def test_ratquad_general_alpha_tends_to_rbf():
+    """The alpha = 1 member used here belongs to the family (1 + r^2/(2 alpha))^-alpha,
+    which tends to exp(-r^2/2) as alpha grows."""
+    r2 = np.linspace(0.0, 9.0, 19)
+    fam = lambda a: (1.0 + r2 / (2.0 * a)) ** (-a)
+    np.testing.assert_allclose(fam(1.0), kernels.k_of_r2(kernels.RATQUAD, r2, 1.0), rtol=1e-15)
+    rbf = kernels.k_of_r2(kernels.RBF, r2, 1.0)
+    assert np.abs(fam(1e6) - rbf).max() < 1e-4 < np.abs(fam(1.0) - rbf).max()
