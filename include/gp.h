@@ -57,11 +57,13 @@ typedef enum {
 } gp_status;
 
 /* Sec. 5 "Experimental Setup": RBF and Matern kernels with output scale s = k(x,x),
- * lengthscales l_j and noise sigma^2.  r^2 = sum_j ((x_j - x'_j)/l_j)^2 and
+ * lengthscales l_j and noise sigma^2; the rational quadratic kernel of the synthetic
+ * study (Tab. S1).  r^2 = sum_j ((x_j - x'_j)/l_j)^2 and
  *   RBF       s exp(-r^2/2)
  *   MATERN32  s (1 + sqrt3 r) exp(-sqrt3 r)
- *   MATERN52  s (1 + sqrt5 r + 5r^2/3) exp(-sqrt5 r)                              */
-typedef enum { GP_RBF = 0, GP_MATERN32 = 3, GP_MATERN52 = 5 } gp_kernel_kind;
+ *   MATERN52  s (1 + sqrt5 r + 5r^2/3) exp(-sqrt5 r)
+ *   RATQUAD   s (1 + r^2/(2 alpha))^-alpha with alpha = 1 (fixed): s / (1 + r^2/2)   */
+typedef enum { GP_RBF = 0, GP_MATERN32 = 3, GP_MATERN52 = 5, GP_RATQUAD = 7 } gp_kernel_kind;
 
 /* Storage and arithmetic of a problem.
  *   GP_FP64  everything in double (kernel MVMs on the FP64 pipe)

@@ -28,7 +28,8 @@ gp_status check_problem(const gp_problem* prob, bool need_data = true) {
   GP_REQUIRE(prob->n >= 1 && prob->n < (int64_t(1) << 31), "n=%lld out of range [1, 2^31)",
              (long long)prob->n);
   GP_REQUIRE(prob->d >= 1 && prob->d <= kMaxD, "d=%d out of range [1, %d]", prob->d, kMaxD);
-  GP_REQUIRE(prob->kind == GP_RBF || prob->kind == GP_MATERN32 || prob->kind == GP_MATERN52,
+  GP_REQUIRE(prob->kind == GP_RBF || prob->kind == GP_MATERN32 || prob->kind == GP_MATERN52 ||
+                 prob->kind == GP_RATQUAD,
              "unknown kernel kind %d", prob->kind);
   GP_REQUIRE(prob->precision >= GP_FP64 && prob->precision <= GP_BF16, "unknown precision %d",
              prob->precision);

@@ -107,6 +107,7 @@ template <class T>
 __device__ __forceinline__ T kval(int kind, T r2, T s) {
   r2 = r2 > T(0) ? r2 : T(0);
   if (kind == GP_RBF) return s * M<T>::ex(T(-0.5) * r2);
+  if (kind == GP_RATQUAD) return s / (T(1) + T(0.5) * r2);
   T r = M<T>::sq(r2);
   if (kind == GP_MATERN32) {
     T ar = T(1.7320508075688772) * r;
@@ -123,6 +124,12 @@ __device__ __forceinline__ void kval_fac(int kind, T r2, T s, T& k, T& fac) {
   if (kind == GP_RBF) {
     k = s * M<T>::ex(T(-0.5) * r2);
     fac = k;
+    return;
+  }
+  if (kind == GP_RATQUAD) {
+    const T q = T(1) / (T(1) + T(0.5) * r2);
+    k = s * q;
+    fac = k * q;
     return;
   }
   T r = M<T>::sq(r2);

@@ -101,6 +101,13 @@ __device__ __forceinline__ void kf_from_s(float sv, float& kv, float& fv) {
     fv = kv;
     return;
   }
+  if (KIND == GP_RATQUAD) {   // alpha = 1: k/s = 1 / (1 - S), fac/s = (k/s)^2
+    float q;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(1.0f - fminf(sv, 0.0f)));
+    kv = q;
+    fv = q * q;
+    return;
+  }
   const float r2 = fmaxf(-2.0f * sv, 0.0f);
   const float r = sqrtf(r2);
   const float L2E = 1.4426950408889634f;
@@ -364,6 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_tc_kernel(GradArgs g) {
         float gs;
         if (g.kind == GP_RBF) gs = h_from_sm<GP_RBF>(sv, mv, hh, hl);
         else if (g.kind == GP_MATERN32) gs = h_from_sm<GP_MATERN32>(sv, mv, hh, hl);
+        else if (g.kind == GP_RATQUAD) gs = h_from_sm<GP_RATQUAD>(sv, mv, hh, hl);
         else gs = h_from_sm<GP_MATERN52>(sv, mv, hh, hl);
         gacc += (double)gs;
         // GEMM_R of the previous tile has read H

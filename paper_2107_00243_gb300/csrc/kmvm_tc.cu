@@ -105,9 +105,17 @@ struct __align__(8) Bars {
 };
 
 // k(r) / s from the exponent tile value S (see the header).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <int KIND>
 __device__ __forceinline__ float kernel_from_s(float sv) {
   if (KIND == GP_RBF) return ex2(sv);
+  // rational quadratic (alpha = 1): 1 / (1 + r^2/2) = 1 / (1 - S), S <= 0
+  if (KIND == GP_RATQUAD) return rcp_approx(1.0f - fminf(sv, 0.0f));
   const float r2 = fmaxf(-2.0f * sv, 0.0f);
   const float r = sqrtf(r2);
   const float L2E = 1.4426950408889634f;
@@ -439,6 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
           uint32_t pk[16], pl[16];
           if (g.kind == GP_RBF) p_from_s<GP_RBF>(v, pk, pl, split);
           else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v, pk, pl, split);
+          else if (g.kind == GP_RATQUAD) p_from_s<GP_RATQUAD>(v, pk, pl, split);
           else p_from_s<GP_MATERN52>(v, pk, pl, split);
           if (c == 0 && wait_p &&
               !mbar_wait(smem_u32(&bars->p_free[fb]), p_par, abort, g.err, 33)) {

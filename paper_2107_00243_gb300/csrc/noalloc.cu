@@ -48,7 +48,8 @@ extern "C" gp_status gp_kernel_mvm_noalloc(const gp_problem* prob, const void* V
   GP_REQUIRE(prob != nullptr, "problem is NULL");
   GP_REQUIRE(prob->n >= 1 && prob->n < (int64_t(1) << 31), "n out of range");
   GP_REQUIRE(prob->d >= 1 && prob->d <= kMaxD, "d=%d out of range [1, %d]", prob->d, kMaxD);
-  GP_REQUIRE(prob->kind == GP_RBF || prob->kind == GP_MATERN32 || prob->kind == GP_MATERN52,
+  GP_REQUIRE(prob->kind == GP_RBF || prob->kind == GP_MATERN32 || prob->kind == GP_MATERN52 ||
+                 prob->kind == GP_RATQUAD,
              "unknown kernel kind %d", prob->kind);
   GP_REQUIRE(prob->precision == GP_FP64 || prob->precision == GP_FP32,
              "gp_kernel_mvm_noalloc supports GP_FP64 and GP_FP32 only");

@@ -20,7 +20,7 @@ from . import build as _build
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "gp.h")
 
-RBF, MATERN32, MATERN52 = 0, 3, 5
+RBF, MATERN32, MATERN52, RATQUAD = 0, 3, 5, 7
 FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 FN_KERNEL_MVM, FN_KERNEL_GRAD_MVM, FN_PIVCHOL, FN_MBCG, FN_MLL_AND_GRAD = range(5)
 STATUS = {0: "GP_OK", 1: "GP_WARN_NOT_CONVERGED", 2: "GP_WARN_RANK_DEFICIENT",

@@ -31,7 +31,7 @@ import math
 
 import numpy as np
 
-RBF, MATERN32, MATERN52 = 0, 3, 5
+RBF, MATERN32, MATERN52, RATQUAD = 0, 3, 5, 7
 FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 
 

@@ -79,6 +79,10 @@ PROBLEMS = {
     "matern32_iso_d4": lambda: workloads.random_problem(1111, 4, kind=kernels.MATERN32,
                                                         ard=False, seed=3, s2=0.01, k=20,
                                                         n_probes=8, tol=1e-3, max_iter=500),
+    # the rational quadratic kernel of the synthetic study (alpha = 1), ARD, d = 3
+    "ratquad_ard_d3": lambda: workloads.random_problem(1500, 3, kind=kernels.RATQUAD,
+                                                       ard=True, seed=9, s2=0.02, k=20,
+                                                       n_probes=8, tol=1e-3, max_iter=500),
     "rbf_iso_d3": lambda: workloads.random_problem(777, 3, kind=kernels.RBF, ard=False,
                                                    seed=5, s2=0.05, k=12, n_probes=6,
                                                    tol=1e-4, max_iter=400),
