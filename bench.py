@@ -466,6 +466,64 @@ def run_c4(args):
     print(json.dumps(line), flush=True)
 
 
+def run_synthetic(args):
+    """The bias / variance study of the paper's synthetic experiment (Tab. S1): n = 10,000
+    points, d in {1, 2, 3}, RBF, Matern-3/2 and rational quadratic kernels, l = 128
+    probes, 25 probe seeds, with no preconditioner (k = 0) and with a rank-128 pivoted
+    Cholesky preconditioner.  Relative bias |mean - exact| / |exact| and relative
+    variance var / exact^2 of the MLL estimate and of each gradient entry (lengthscale,
+    output scale, noise) against the exact values of
+    tests/golden/synthetic_study_exact.json (dense Cholesky, FP64 oracle).  k = 0 runs
+    in FP32 (CG tol 1e-5: its errors are 1e-5 and larger), k = 128 in FP64 (CG tol 1e-10).
+    Prints one JSON line per (kernel, d, k) and a markdown table."""
+    import numpy as np
+    import torch
+    from paper_2107_00243_gb300 import build, gp, workloads
+    build.build()
+    gp.load()
+    with open(os.path.join(ROOT, "tests", "golden", "synthetic_study_exact.json")) as f:
+        exact = json.load(f)["problems"]
+    names = {workloads.RBF: "RBF", workloads.MATERN32: "Matern32", workloads.RATQUAD: "RatQuad"}
+    seeds = args.reps if args.reps and args.reps > 3 else 25
+    rows = []
+    for kind in (workloads.MATERN32, workloads.RBF, workloads.RATQUAD):
+        for d in (1, 2, 3):
+            p = workloads.synthetic_study(kind, d)
+            ex = exact[f"{kind}_{d}"]
+            ref = np.array([ex["mll"]] + ex["grad"])
+            for k, prec, tol in ((0, gp.FP32, 1e-5), (128, gp.FP64, 1e-10)):
+                prob = gp.Problem(p.X, p.theta, p.kind, p.ard, prec)
+                ws = gp.Workspace()
+                vals, its, t0 = [], [], time.perf_counter()
+                for sd in range(seeds):
+                    o = gp.opts(cg_tol=tol, max_iter=1000, recompute_every=50, seed=sd)
+                    st, out, iout = gp.gp_mll_and_grad(prob, p.y, k, p.n_probes, o, workspace=ws)
+                    r = gp.unpack(out, iout, prob.p, p.n_probes, k)
+                    vals.append([r["mll"]] + list(r["grad"]))
+                    its.append(int(r["iters"].max()))
+                vals = np.array(vals)
+                bias = np.abs(vals.mean(0) - ref) / np.abs(ref)
+                var = vals.var(0, ddof=1) / ref ** 2
+                row = {"kernel": names[kind], "d": d, "k": k, "n_probes": p.n_probes,
+                       "precision": "fp64" if prec == gp.FP64 else "fp32", "seeds": seeds,
+                       "bias": {"mll": bias[0], "lengthscale": bias[1], "outputscale": bias[2],
+                                "noise": bias[3]},
+                       "var": {"mll": var[0], "lengthscale": var[1], "outputscale": var[2],
+                               "noise": var[3]},
+                       "cg_iters_max": max(its), "s": time.perf_counter() - t0}
+                rows.append(row)
+                print(json.dumps(row), flush=True)
+    print("| kernel | d | k | MLL bias | MLL var | d/ds bias | d/ds var | d/dl bias | d/dl var "
+          "| d/dsigma2 bias | d/dsigma2 var | CG its |")
+    print("|---|---|---|---|---|---|---|---|---|---|---|---|")
+    for r in rows:
+        b, v = r["bias"], r["var"]
+        print(f"| {r['kernel']} | {r['d']} | {r['k']} | {b['mll']:.0e} | {v['mll']:.0e} | "
+              f"{b['outputscale']:.0e} | {v['outputscale']:.0e} | {b['lengthscale']:.0e} | "
+              f"{v['lengthscale']:.0e} | {b['noise']:.0e} | {v['noise']:.0e} | "
+              f"{r['cg_iters_max']} |")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,7 +535,7 @@ def main():
                     help="timed steps of the plain FP32 form when --precision is mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg", "grad", "batched", "peaks",
-                                       "c4"],
+                                       "c4", "synthetic"],
                     default="estimator",
                     help="kmvm / mbcg / grad: time only the kernel product, a short CG call "
                          "or the gradient contraction on an instance of the workload (for "
@@ -493,6 +551,9 @@ def main():
         return
     if args.case == "c4":
         run_c4(args)
+        return
+    if args.case == "synthetic":
+        run_synthetic(args)
         return
     if args.case != "estimator":
         run_case(args)

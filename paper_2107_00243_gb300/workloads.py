@@ -159,6 +159,19 @@ def c5_batched(n_problems=64, seed=0, n_lo=2000, n_hi=50000):
     return probs
 
 
+def synthetic_study(kind, d, n=10000, seed=0):
+    """The synthetic data of the bias / variance study (Tab. S1): n points uniform on
+    [0, 1]^d, targets sum_j sin(2 pi x_j) / sqrt(d) plus N(0, sigma^2) noise with
+    sigma^2 = 1e-2 (the paper's value).  The paper prints no lengthscale or output
+    scale; an isotropic lengthscale of 0.2 and s = 1 are used."""
+    rng = np.random.default_rng(seed + 101 * d + kind)
+    X = rng.uniform(0.0, 1.0, (n, d))
+    y = np.sin(2.0 * np.pi * X).sum(1) / math.sqrt(d) + 0.1 * rng.standard_normal(n)
+    theta = np.array([0.2, 1.0, 1e-2])
+    return Problem(f"synthetic_study[kind={kind},d={d}]", X, y, theta, kind, False, k=128,
+                   n_probes=128, tol=1e-10, max_iter=2000, precision=FP64, seed=seed)
+
+
 def subsample(prob, n, seed=1):
     """A smaller problem drawn from the same workload (rows chosen at random)."""
     if n >= prob.n:
