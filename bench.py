@@ -475,6 +475,8 @@ def run_synthetic(args):
     output scale, noise) against the exact values of
     tests/golden/synthetic_study_exact.json (dense Cholesky, FP64 oracle).  k = 0 runs
     in FP32 (CG tol 1e-5: its errors are 1e-5 and larger), k = 128 in FP64 (CG tol 1e-10).
+    Where K is numerically low-rank (d = 1, and d = 2 for the smooth kernels) the factor
+    stops below 128 at the FP64 rounding floor of its residual; the rank column shows it.
     Prints one JSON line per (kernel, d, k) and a markdown table."""
     import numpy as np
     import torch
@@ -494,13 +496,14 @@ def run_synthetic(args):
             for k, prec, tol in ((0, gp.FP32, 1e-5), (128, gp.FP64, 1e-10)):
                 prob = gp.Problem(p.X, p.theta, p.kind, p.ard, prec)
                 ws = gp.Workspace()
-                vals, its, t0 = [], [], time.perf_counter()
+                vals, its, ranks, t0 = [], [], [], time.perf_counter()
                 for sd in range(seeds):
                     o = gp.opts(cg_tol=tol, max_iter=1000, recompute_every=50, seed=sd)
                     st, out, iout = gp.gp_mll_and_grad(prob, p.y, k, p.n_probes, o, workspace=ws)
                     r = gp.unpack(out, iout, prob.p, p.n_probes, k)
                     vals.append([r["mll"]] + list(r["grad"]))
                     its.append(int(r["iters"].max()))
+                    ranks.append(r["rank"])
                 vals = np.array(vals)
                 bias = np.abs(vals.mean(0) - ref) / np.abs(ref)
                 var = vals.var(0, ddof=1) / ref ** 2
@@ -510,15 +513,16 @@ def run_synthetic(args):
                                 "noise": bias[3]},
                        "var": {"mll": var[0], "lengthscale": var[1], "outputscale": var[2],
                                "noise": var[3]},
-                       "cg_iters_max": max(its), "s": time.perf_counter() - t0}
+                       "rank": max(ranks), "cg_iters_max": max(its),
+                       "s": time.perf_counter() - t0}
                 rows.append(row)
                 print(json.dumps(row), flush=True)
-    print("| kernel | d | k | MLL bias | MLL var | d/ds bias | d/ds var | d/dl bias | d/dl var "
-          "| d/dsigma2 bias | d/dsigma2 var | CG its |")
+    print("| kernel | d | k (rank) | MLL bias | MLL var | d/ds bias | d/ds var | d/dl bias "
+          "| d/dl var | d/dsigma2 bias | d/dsigma2 var | CG its |")
     print("|---|---|---|---|---|---|---|---|---|---|---|---|")
     for r in rows:
         b, v = r["bias"], r["var"]
-        print(f"| {r['kernel']} | {r['d']} | {r['k']} | {b['mll']:.0e} | {v['mll']:.0e} | "
+        print(f"| {r['kernel']} | {r['d']} | {r['k']} ({r['rank']}) | {b['mll']:.0e} | {v['mll']:.0e} | "
               f"{b['outputscale']:.0e} | {v['outputscale']:.0e} | {b['lengthscale']:.0e} | "
               f"{v['lengthscale']:.0e} | {b['noise']:.0e} | {v['noise']:.0e} | "
               f"{r['cg_iters_max']} |")

@@ -160,10 +160,13 @@ gp_status gp_kernel_grad_mvm(const gp_problem* prob, const void* V, int64_t ldv,
  * approximation quality", after Harbrecht et al. 2012):
  *   pi_m = argmax of the residual diagonal (lowest index on ties, FP64),
  *   L[:, m] = (K[:, pi_m] - L[:, :m] L[pi_m, :m]^T) / sqrt(d_{pi_m}).
- * Stops early when the residual trace <= tol * tr K or the best residual <= 0.
+ * Stops early when the residual trace <= tol * tr K, or when the best residual
+ * <= n u max_i K_ii (u = 2^-24 for FP32, 2^-53 for FP64: LAPACK xPSTRF's default
+ * rank rule; below it the residual is rounding error of the earlier columns).
  * Outputs: L (n x k column-major, ld ldl; columns >= rank are zero), piv (k int32,
  * entries >= rank are -1), rank_out (1 int32).  piv_override (device, k int32, or
- * NULL) forces the pivot order.  Asynchronous.                                    */
+ * NULL) forces the pivot order; an entry outside [0, n) stops the factor there
+ * (pad a shorter order with -1).  Asynchronous.                                   */
 gp_status gp_pivchol(const gp_problem* prob, int32_t k, double tol,
                      const int32_t* piv_override, void* L, int64_t ldl, int32_t* piv,
                      int32_t* rank_out, void* ws, size_t ws_bytes, gp_stream_t stream);
@@ -217,10 +220,11 @@ gp_status gp_mbcg(const gp_problem* prob, const void* L, int64_t ldl, int32_t k,
  *   grad = GK + 1/2 PROBEP - 1/2 TRP.
  * y: n reals.  eps_override (device, (k + n) x n_probes int8 +-1 column-major with
  * leading dim k + n: rows 0..k-1 eps1, rows k.. eps2; or NULL = SplitMix64 from
- * opts->seed), piv_override (k int32 or NULL), iters_override (t int32 or NULL)
- * exist for parity testing.  out: GP_OUT_LEN(p, n_probes) doubles; iout:
- * GP_IOUT_LEN(k, t) int32.  Synchronises with `stream`, except while `stream` is
- * being captured into a CUDA graph: then nothing is read back, mBCG's iteration
+ * opts->seed), piv_override (k int32 or NULL; -1 entries stop the factor),
+ * iters_override (t int32 or NULL) exist for parity testing.
+ * out: GP_OUT_LEN(p, n_probes) doubles; iout: GP_IOUT_LEN(k, t) int32.
+ * Synchronises with `stream`, except while `stream` is being captured into a CUDA
+ * graph: then nothing is read back, mBCG's iteration
  * loop is recorded as a conditional WHILE node (the stopping rule is evaluated on
  * the device), the call returns GP_OK, and the status of the evaluation is
  * iout[GP_IOUT_STATUS] once the graph has run.                                   */

@@ -28,6 +28,8 @@ Readings of the paper used here (the paper is silent or ambiguous on these):
 * Alg. 2 solves K_hat^-1 (dK_hat z_i) per hyperparameter; by symmetry
   z^T K^-1 dK w = (K^-1 z)^T dK w, so the probe solves of the forward pass are reused.
 * dK_hat uses the noise too (dK_hat/dsigma^2 = I).
+* ``rank_floor`` stops the pivoted Cholesky at a residual of rank_floor * max K_ii
+  (pivchol.py); a comparison with a factor formed in precision u passes n u.
 * dP_hat is taken at frozen pivots (woodbury.NystromDerivative).
 """
 import numpy as np
@@ -37,14 +39,14 @@ from . import kernels, lanczos, mbcg, pivchol, probes, woodbury
 
 def mll_and_grad(kind, X, y, theta, ard, k, n_probes, tol, max_iter, seed=0,
                  recompute_every=0, pivchol_tol=0.0, piv_override=None,
-                 iters_override=None, eps=None, literal=False, with_grad=True):
+                 iters_override=None, eps=None, literal=False, with_grad=True, rank_floor=0.0):
     X = np.asarray(X, np.float64)
     y = np.asarray(y, np.float64)
     n = X.shape[0]
     op = kernels.KernelOperator(kind, X, theta, ard)
     s2 = op.s2
 
-    L, piv, rank, _ = pivchol.pivoted_cholesky(op, k, pivchol_tol, piv_override)
+    L, piv, rank, _ = pivchol.pivoted_cholesky(op, k, pivchol_tol, piv_override, rank_floor)
     logdetP = woodbury.logdet(L, s2)
 
     if eps is None:

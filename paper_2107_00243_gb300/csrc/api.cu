@@ -97,7 +97,7 @@ void plan_piv(Arena& A, const Prob& pb, int k, PivPlan& P) {
   P.b.pidx = A.take<int>(kPivBlocks);
   P.b.psum = A.take<double>(kPivBlocks);
   P.b.dval = A.take<double>((size_t)k + 2);
-  P.b.trace0 = A.take<double>(1);
+  P.b.trace0 = A.take<double>(2);
   P.b.stop = A.take<int>(1);
   P.b.counter = A.take<unsigned>(4);
 }

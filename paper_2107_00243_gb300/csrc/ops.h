@@ -100,7 +100,7 @@ struct PivBufs {
   int* pidx;         // per block best index
   double* psum;      // per block residual sum
   double* dval;      // k + 1: residual diagonal of each pivot
-  double* trace0;    // 1
+  double* trace0;    // 2: tr K and max_i K_ii of the initial diagonal
   int* stop;         // 1
   unsigned* counter; // 1
 };

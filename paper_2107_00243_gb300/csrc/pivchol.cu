@@ -11,7 +11,14 @@
 //      block reduction whose partials the last block to finish combines in block
 //      order (deterministic).
 // The stopping tests (rank k reached, residual trace <= tol * tr K, best residual
-// <= 0) are taken on the device; later step kernels see the stop flag and return.
+// <= n u max_i K_ii) are taken on the device; later step kernels see the stop flag
+// and return.  The last test is the default rank rule of LAPACK's pivoted Cholesky
+// (xPSTRF; Lucas, "LAPACK-style codes for level 2 and 3 pivoted Cholesky
+// factorizations", 2004), with u the unit roundoff of the precision L is formed in
+// (2^-24 for FP32, 2^-53 for FP64).  A residual below it is rounding error of the
+// earlier columns: the column it would normalise is noise, and the frozen-pivot
+// derivative of the factor (L = K[:, piv] L[piv, :]^-T) no longer holds for it.
+// The factor stops there with rank < k and the caller reports the rank deficiency.
 #include "ops.h"
 
 namespace gp {
@@ -56,10 +63,11 @@ __device__ Best block_best(Best x, double* sv, int* si) {
 }
 
 // Final combine for step m (or the initial diagonal, m = -1): choose pivot m+1.
-__device__ void choose_next(int64_t n, int m, int k, double tol, const int* piv_override,
-                            const double* dres, const double* pval, const int* pidx,
-                            const double* psum, int nblk, int* piv, double* dval,
-                            double* trace0, int* stop, int* rank) {
+// trace0 = {tr K, max_i K_ii}, both of the initial diagonal; floor_rel = n u.
+__device__ void choose_next(int64_t n, int m, int k, double tol, double floor_rel,
+                            const int* piv_override, const double* dres, const double* pval,
+                            const int* pidx, const double* psum, int nblk, int* piv,
+                            double* dval, double* trace0, int* stop, int* rank) {
   if (threadIdx.x != 0) return;
   Best b{-1.0, -1};
   double sum = 0.0;
@@ -67,13 +75,16 @@ __device__ void choose_next(int64_t n, int m, int k, double tol, const int* piv_
     b = better(b, Best{pval[q], pidx[q]});
     sum += psum[q];
   }
-  if (m < 0) *trace0 = sum;
+  if (m < 0) {
+    trace0[0] = sum;
+    trace0[1] = b.v;
+  }
   const int next = m + 1;
   if (next >= k) { *rank = k; *stop = 1; return; }
-  if (sum <= tol * (*trace0)) { *rank = next; *stop = 1; return; }
+  if (sum <= tol * trace0[0]) { *rank = next; *stop = 1; return; }
   int pi = piv_override ? piv_override[next] : b.i;
   double dv = (pi >= 0 && pi < n) ? dres[pi] : -1.0;   // an out-of-range override stops
-  if (!(dv > 0.0)) { *rank = next; *stop = 1; return; }
+  if (!(dv > 0.0) || dv <= floor_rel * trace0[1]) { *rank = next; *stop = 1; return; }
   piv[next] = pi;
   dval[next] = dv;
   *rank = next + 1;   // provisional: column `next` will be formed
@@ -82,7 +93,7 @@ __device__ void choose_next(int64_t n, int m, int k, double tol, const int* piv_
 template <class T>
 __global__ void __launch_bounds__(kThreads) pivchol_init(
     int64_t n, int d, int kind, int D, const double* __restrict__ theta, int k, double tol,
-    const int* __restrict__ piv_override, PivBufs b, int* piv, int* rank) {
+    double floor_rel, const int* __restrict__ piv_override, PivBufs b, int* piv, int* rank) {
   __shared__ double sv[32];
   __shared__ int si[32];
   const double s = theta[D];
@@ -105,15 +116,16 @@ __global__ void __launch_bounds__(kThreads) pivchol_init(
   }
   if (last_block_arrived(b.counter)) {
     if (threadIdx.x == 0) *b.stop = 0;
-    choose_next(n, -1, k, tol, piv_override, b.dres, b.pval, b.pidx, b.psum, gridDim.x, piv,
-                b.dval, b.trace0, b.stop, rank);
+    choose_next(n, -1, k, tol, floor_rel, piv_override, b.dres, b.pval, b.pidx, b.psum,
+                gridDim.x, piv, b.dval, b.trace0, b.stop, rank);
   }
 }
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) pivchol_step(
     int64_t n, int d, int kind, int D, const double* __restrict__ theta, int m, int k,
-    double tol, const int* __restrict__ piv_override, const T* __restrict__ Xs,
+    double tol, double floor_rel, const int* __restrict__ piv_override,
+    const T* __restrict__ Xs,
     T* __restrict__ L, int64_t ldl, PivBufs b, int* piv, int* rank) {
   if (*b.stop) return;
   extern __shared__ unsigned char smem_raw[];
@@ -169,8 +181,8 @@ __global__ void __launch_bounds__(kThreads) pivchol_step(
     b.psum[blockIdx.x] = bs;
   }
   if (last_block_arrived(b.counter))
-    choose_next(n, m, k, tol, piv_override, b.dres, b.pval, b.pidx, b.psum, gridDim.x, piv,
-                b.dval, b.trace0, b.stop, rank);
+    choose_next(n, m, k, tol, floor_rel, piv_override, b.dres, b.pval, b.pidx, b.psum,
+                gridDim.x, piv, b.dval, b.trace0, b.stop, rank);
 }
 
 }  // namespace
@@ -192,13 +204,15 @@ gp_status pivchol_run(const Prob& pb, const void* Xs_, int k, double tol, const 
   GP_CUDA_TRY(cudaMemsetAsync(rank, 0, sizeof(int), st));
   if (k == 0) return GP_OK;
   const int blocks = (int)std::min<int64_t>(kPivBlocks, cdiv(pb.n, kThreads));
+  const double floor_rel = (double)pb.n * (sizeof(T) == 4 ? 0x1p-24 : 0x1p-53);
   pivchol_init<T><<<blocks, kThreads, 0, st>>>(pb.n, pb.d, pb.kind, pb.D, pb.theta, k, tol,
-                                                piv_override, b, piv, rank);
+                                                floor_rel, piv_override, b, piv, rank);
   GP_LAUNCH_CHECK();
   for (int m = 0; m < k; ++m) {
     size_t sm = sizeof(T) * (size_t)(m > 0 ? m : 1);
     pivchol_step<T><<<blocks, kThreads, sm, st>>>(pb.n, pb.d, pb.kind, pb.D, pb.theta, m, k,
-                                                   tol, piv_override, Xs, L, ldl, b, piv, rank);
+                                                   tol, floor_rel, piv_override, Xs, L, ldl, b,
+                                                   piv, rank);
     GP_LAUNCH_CHECK();
   }
   return GP_OK;

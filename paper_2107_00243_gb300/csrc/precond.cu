@@ -231,12 +231,18 @@ __global__ void gather_lpi(int k, const T* __restrict__ L, int64_t ldl,
   Lpi[e] = v;
 }
 
-// B1 = tmp - sigma^2 B1
-__global__ void combine_b1(int64_t elems, const double* __restrict__ tmp,
-                           const double* __restrict__ theta, int D, double* __restrict__ B1) {
+// E = I - sigma^2 C^-1 (= C^-1 L^T L, k x k row-major).  Both terms are O(1), so the
+// difference is accurate to rounding of 1; B1 is then formed as L_pi^-T E L_pi^-1.
+// The other order, W^-1 - sigma^2 L_pi^-T C^-1 L_pi^-1, subtracts two matrices whose
+// entries grow like 1 / (smallest pivot residual) and loses every digit of B1 once the
+// factor nears numerical rank deficiency.
+__global__ void eye_minus_s2_cinv(int k, const double* __restrict__ Cinv,
+                                  const double* __restrict__ theta, int D,
+                                  double* __restrict__ E) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= elems) return;
-  B1[e] = tmp[e] - theta[D + 1] * B1[e];
+  if (e >= (int64_t)k * k) return;
+  const int i = (int)(e / k), j = (int)(e % k);
+  E[e] = (i == j ? 1.0 : 0.0) - theta[D + 1] * Cinv[e];
 }
 
 // One block per hyperparameter q: the FP64 contractions listed at the top.
@@ -334,11 +340,11 @@ gp_status precond_terms(const Prob& pb, const void* Xs_, const T* L, int64_t ldl
     GP_LAUNCH_CHECK();
     GP_TRY(tri_inv_lower(k, b.Lpi, b.Lpinv, st));
     GP_TRY(gemm64(k, k, k, b.Lpinv, 1, Cinv, 0, b.A1, 1.0, 0.0, st));       // L_pi^-T C^-1
-    GP_TRY(gemm64(k, k, k, b.Lpinv, 1, b.Lpinv, 0, b.tmp, 1.0, 0.0, st));  // W^-1
-    GP_TRY(gemm64(k, k, k, b.A1, 0, b.Lpinv, 0, b.B1, 1.0, 0.0, st));      // L_pi^-T C^-1 L_pi^-1
-    combine_b1<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, b.tmp,
-                                                                   pb.theta, pb.D, b.B1);
+    eye_minus_s2_cinv<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, Cinv, pb.theta,
+                                                                          pb.D, b.B1);
     GP_LAUNCH_CHECK();
+    GP_TRY(gemm64(k, k, k, b.Lpinv, 1, b.B1, 0, b.tmp, 1.0, 0.0, st));     // L_pi^-T E
+    GP_TRY(gemm64(k, k, k, b.tmp, 0, b.Lpinv, 0, b.B1, 1.0, 0.0, st));     // L_pi^-T E L_pi^-1
     T* Bt = reinterpret_cast<T*>(b.Q);                 // k x k then l x k, problem precision
     T* Z1 = reinterpret_cast<T*>(b.part);              // n x k
     T* Z2 = Z1 + (size_t)pb.n * k;                     // n x k

@@ -264,6 +264,17 @@ def gp_kernel_grad_mvm(prob, V, workspace=None):
     return dW.transpose(1, 2)
 
 
+def _piv_override(piv_override, k, device):
+    """k int32 pivots for the device: a shorter order is padded with -1 (an entry
+    outside [0, n) stops the factor there); a longer one is an error."""
+    po = torch.as_tensor(piv_override, dtype=torch.int32).reshape(-1)
+    if po.numel() > max(k, 0):
+        raise ValueError(f"piv_override has {po.numel()} entries, more than k = {k}")
+    if po.numel() < k:
+        po = torch.cat([po, torch.full((k - po.numel(),), -1, dtype=torch.int32)])
+    return po.to(device).contiguous()
+
+
 def gp_pivchol(prob, k, tol=0.0, piv_override=None, workspace=None):
     """Returns (L (n, k), piv (k,) int32, rank int tensor)."""
     lib = load()
@@ -271,8 +282,8 @@ def gp_pivchol(prob, k, tol=0.0, piv_override=None, workspace=None):
     piv = torch.empty(max(k, 1), dtype=torch.int32, device=prob.device)
     rank = torch.empty(1, dtype=torch.int32, device=prob.device)
     po = None
-    if piv_override is not None:
-        po = torch.as_tensor(piv_override, dtype=torch.int32).to(prob.device).contiguous()
+    if piv_override is not None and k > 0:
+        po = _piv_override(piv_override, k, prob.device)
     ws = (workspace or _WS).get(gp_workspace_size(FN_PIVCHOL, prob.n, prob.d, k, 1,
                                                   prob.precision), prob.device)
     _check("gp_pivchol", lib.gp_pivchol(prob.cref(), k, float(tol), _ptr(po), _ptr(L), prob.n,
@@ -296,7 +307,10 @@ def gp_mbcg(prob, L, B, o, iters_override=None, workspace=None):
     status = torch.empty(1, dtype=torch.int32, device=prob.device)
     io = None
     if iters_override is not None:
-        io = torch.as_tensor(iters_override, dtype=torch.int32).to(prob.device).contiguous()
+        io = torch.as_tensor(iters_override, dtype=torch.int32).reshape(-1)
+        if io.numel() != t:
+            raise ValueError(f"iters_override has {io.numel()} entries, not t = {t}")
+        io = io.to(prob.device).contiguous()
     ws = (workspace or _WS).get(gp_workspace_size(FN_MBCG, prob.n, prob.d, k, t, prob.precision,
                                                   o.max_iter), prob.device)
     st = _check("gp_mbcg", lib.gp_mbcg(prob.cref(), _ptr(Lc), prob.n, k, _ptr(Bc), prob.n, t,
@@ -323,12 +337,19 @@ def gp_mll_and_grad(prob, y, k, n_probes, o, eps_override=None, piv_override=Non
         iout = torch.empty(2 + t + max(k, 1), dtype=torch.int32, device=prob.device)
     eo = po = io = None
     if eps_override is not None:
-        eo = torch.as_tensor(eps_override).to(device=prob.device, dtype=torch.int8)
+        eo = torch.as_tensor(eps_override)
+        if tuple(eo.shape) != (k + prob.n, n_probes):
+            raise ValueError(f"eps_override has shape {tuple(eo.shape)}, not "
+                             f"(k + n, n_probes) = {(k + prob.n, n_probes)}")
+        eo = eo.to(device=prob.device, dtype=torch.int8)
         eo = eo.t().contiguous()          # ((k + n), l) column-major
-    if piv_override is not None:
-        po = torch.as_tensor(piv_override, dtype=torch.int32).to(prob.device).contiguous()
+    if piv_override is not None and k > 0:
+        po = _piv_override(piv_override, k, prob.device)
     if iters_override is not None:
-        io = torch.as_tensor(iters_override, dtype=torch.int32).to(prob.device).contiguous()
+        io = torch.as_tensor(iters_override, dtype=torch.int32).reshape(-1)
+        if io.numel() != t:
+            raise ValueError(f"iters_override has {io.numel()} entries, not t = {t}")
+        io = io.to(prob.device).contiguous()
     ws = (workspace or _WS).get(gp_workspace_size(FN_MLL_AND_GRAD, prob.n, prob.d, k, t,
                                                   prob.precision, o.max_iter), prob.device)
     st = _check("gp_mll_and_grad",

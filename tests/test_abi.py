@@ -47,7 +47,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert r == -1 and b"n=0" in lib.gp_last_error_message()
     P = gp._Problem(10, 40, 0, 1, gp.FP32, 1, 1)        # d too large
     assert lib.gp_kernel_mvm(ctypes.byref(P), 8, 10, 1, 16, 10, None, 0, None) == -1
-    P = gp._Problem(10, 3, 7, 1, gp.FP32, 1, 1)         # unknown kernel
+    P = gp._Problem(10, 3, 42, 1, gp.FP32, 1, 1)        # unknown kernel
     assert lib.gp_kernel_mvm(ctypes.byref(P), 8, 10, 1, 16, 10, None, 0, None) == -1
     P = gp._Problem(10, 3, 0, 1, gp.FP32, 1, 1)
     assert lib.gp_kernel_mvm(ctypes.byref(P), 8, 10, 1, 8, 10, None, 0, None) == -1  # W aliases V
@@ -78,3 +78,15 @@ def test_batched_workspace_size_is_sum_of_aligned_slices():
     lib = gp.load()
     assert lib.gp_workspace_size_batched(len(shapes), arr, k, nl, mi) == want
     assert lib.gp_workspace_size_batched(0, arr, k, nl, mi) == 0
+
+
+def test_override_marshalling():
+    """A pivot order shorter than k is padded with -1 (which stops the factor on the
+    device), a longer one is rejected before any device call."""
+    import numpy as np
+    import torch
+    po = gp._piv_override([3, 1], 4, "cpu")
+    assert po.dtype == torch.int32 and po.tolist() == [3, 1, -1, -1]
+    assert gp._piv_override(np.array([5, 0, 2]), 3, "cpu").tolist() == [5, 0, 2]
+    with pytest.raises(ValueError):
+        gp._piv_override([0, 1, 2, 3, 4], 4, "cpu")

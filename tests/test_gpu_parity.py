@@ -38,6 +38,7 @@ pytestmark = pytest.mark.gpu
 
 KTOL = {gp.FP64: 1e-11, gp.FP32: 2e-5}
 ETOL = {gp.FP64: (5e-9, 1e-7), gp.FP32: (1e-4, 1e-4)}   # (values, gradient entries)
+GP_WARN_RANK_DEFICIENT = 2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -254,19 +255,46 @@ def _compare(r, ref, tol):
     return errs
 
 
+def _rank_floor(n, prec):
+    """n u of the precision the factor is formed in (the pivoted Cholesky's rank rule)."""
+    return n * (2.0 ** -53 if prec == gp.FP64 else 2.0 ** -24)
+
+
 def _run_matched(p, prec, tol_override=None):
     ref = estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, p.k, p.n_probes, p.tol,
-                                 p.max_iter, seed=p.seed, recompute_every=p.recompute_every)
+                                 p.max_iter, seed=p.seed, recompute_every=p.recompute_every,
+                                 rank_floor=_rank_floor(p.n, prec))
     prob = gp.Problem(p.X, p.theta, p.kind, p.ard, prec)
     o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, recompute_every=p.recompute_every,
                 seed=p.seed)
     st, out, iout = gp.gp_mll_and_grad(prob, p.y, p.k, p.n_probes, o, piv_override=ref["piv"],
                                        iters_override=ref["iters"])
     r = gp.unpack(out, iout, prob.p, p.n_probes, p.k)
-    assert st >= 0 and r["status"] == 0
+    # a factor that stops below k reports GP_WARN_RANK_DEFICIENT
+    assert st == (0 if ref["rank"] == p.k else GP_WARN_RANK_DEFICIENT) and r["status"] == 0
+    assert r["rank"] == ref["rank"]
     np.testing.assert_array_equal(r["iters"], ref["iters"])
-    np.testing.assert_array_equal(r["piv"], ref["piv"])
+    np.testing.assert_array_equal(r["piv"][:ref["rank"]], ref["piv"])
+    assert np.all(r["piv"][ref["rank"]:] == -1)
     return r, ref, _compare(r, ref, tol_override or ETOL[prec])
+
+
+@pytest.mark.parametrize("k", [20, 24, 32])
+@pytest.mark.parametrize("prec", [gp.FP64, gp.FP32])
+def test_estimator_near_numerical_rank_deficiency(prec, k):
+    """The 1-D problem of the synthetic study (n = 1,500, lengthscale 0.2, sigma^2 = 1e-2):
+    the pivot residuals reach 1e-13 after 19 pivots and the FP64 rounding floor
+    (~1e-16) after 21, and fall below the FP32 floor after 10.  The factor stops at
+    n u max K_ii of its precision (the oracle applies the same rule), and the
+    preconditioner terms tr(P^-1 dP) stay within the usual bounds: B1 is formed as
+    L_pi^-T (I - sigma^2 C^-1) L_pi^-1, where the other order lost 3e-3 (k = 20) to 7
+    (k = 32) of the lengthscale entry."""
+    p = workloads.synthetic_study(kernels.RBF, 1, n=1500)
+    p.k, p.n_probes = k, 8
+    p.tol, p.max_iter = (1e-10, 1500) if prec == gp.FP64 else (1e-4, 600)
+    # FP32: K_hat has condition ~1e5 here (sigma^2 = 1e-2 against eigenvalues ~1e3)
+    r, ref, _ = _run_matched(p, prec, tol_override=None if prec == gp.FP64 else (2e-3, 1e-2))
+    assert r["rank"] == (19 if prec == gp.FP64 else 10)
 
 
 def test_estimator_small_rbf_fp64_full_size():

@@ -89,3 +89,38 @@ def test_zero_rank_and_override():
     L2, piv2, r2, _ = pivchol.pivoted_cholesky(op, 6, piv_override=piv1)
     np.testing.assert_array_equal(piv1, piv2)
     np.testing.assert_allclose(L1, L2)
+
+
+@pytest.mark.parametrize("kind", [kernels.RBF, kernels.MATERN32, kernels.RATQUAD])
+@pytest.mark.parametrize("u", [2.0 ** -53, 2.0 ** -24])
+def test_rank_floor_stops_at_exact_rank(kind, u):
+    """r distinct points, each repeated: K has rank exactly r for these strictly
+    positive definite kernels.  After r pivots every residual is rounding error, so
+    with floor = n u the factor stops at rank r; the rank-r factor reproduces K."""
+    r, rep = 9, 7
+    rng = np.random.default_rng(4)
+    Xd = rng.uniform(size=(r, 2))
+    X = np.repeat(Xd, rep, axis=0)[rng.permutation(r * rep)]
+    theta = np.array([0.4, 0.7, 1.3, 0.01])
+    op = kernels.KernelOperator(kind, X, theta, True)
+    n = r * rep
+    L, piv, rank, _ = pivchol.pivoted_cholesky(op, 30, floor=n * u)
+    assert rank == r
+    assert len(set(map(tuple, X[piv]))) == r          # one pivot per distinct point
+    K = kernels.kernel_block(kind, X, X, theta, True)
+    np.testing.assert_allclose(L @ L.T, K, atol=1e-10)
+
+
+def test_rank_floor_zero_is_the_textbook_rule():
+    """floor = 0 keeps the plain rule (stop only at a residual <= 0): the same factor
+    as before the option existed, and a positive floor below every pivot residual
+    changes nothing."""
+    op = _op(80, 3, kernels.MATERN52, seed=6)
+    L0, piv0, r0, t0 = pivchol.pivoted_cholesky(op, 20)
+    L1, piv1, r1, t1 = pivchol.pivoted_cholesky(op, 20, floor=0.0)
+    d = np.diag(L0[piv0]) ** 2
+    L2, piv2, r2, _ = pivchol.pivoted_cholesky(op, 20, floor=0.5 * d.min() / op.diag().max())
+    assert r0 == r1 == r2 == 20
+    np.testing.assert_array_equal(piv0, piv1)
+    np.testing.assert_array_equal(piv0, piv2)
+    np.testing.assert_array_equal(L0, L2)
