@@ -30,23 +30,33 @@ Readings of the paper used here (the paper is silent or ambiguous on these):
 * dK_hat uses the noise too (dK_hat/dsigma^2 = I).
 * ``rank_floor`` stops the pivoted Cholesky at a residual of rank_floor * max K_ii
   (pivchol.py); a comparison with a factor formed in precision u passes n u.
+* ``rff = (eps, g)`` replaces the partial Cholesky factor by random Fourier features
+  (Tab. 2; features.py), k = 2m columns, with dP_hat at frozen draws.
 * dP_hat is taken at frozen pivots (woodbury.NystromDerivative).
 """
 import numpy as np
 
-from . import kernels, lanczos, mbcg, pivchol, probes, woodbury
+from . import features, kernels, lanczos, mbcg, pivchol, probes, woodbury
 
 
 def mll_and_grad(kind, X, y, theta, ard, k, n_probes, tol, max_iter, seed=0,
                  recompute_every=0, pivchol_tol=0.0, piv_override=None,
-                 iters_override=None, eps=None, literal=False, with_grad=True, rank_floor=0.0):
+                 iters_override=None, eps=None, literal=False, with_grad=True, rank_floor=0.0,
+                 rff=None):
     X = np.asarray(X, np.float64)
     y = np.asarray(y, np.float64)
     n = X.shape[0]
     op = kernels.KernelOperator(kind, X, theta, ard)
     s2 = op.s2
 
-    L, piv, rank, _ = pivchol.pivoted_cholesky(op, k, pivchol_tol, piv_override, rank_floor)
+    if rff is None:
+        L, piv, rank, _ = pivchol.pivoted_cholesky(op, k, pivchol_tol, piv_override, rank_floor)
+        dprec = None
+    else:
+        # random Fourier features (features.py): k = 2m columns from the draws (eps, g)
+        dprec = features.RandomFourier(kind, X, theta, ard, *rff)
+        L, piv, rank = dprec.Phi, np.zeros(0, np.int64), dprec.Phi.shape[1]
+        k = rank
     logdetP = woodbury.logdet(L, s2)
 
     if eps is None:
@@ -86,7 +96,7 @@ def mll_and_grad(kind, X, y, theta, ard, k, n_probes, tol, max_iter, seed=0,
 
     Xp = cg["X"][:, 1:]                  # ~ K_hat^-1 z_i
     Wp = cg["z0"][:, 1:]                 # = P_hat^-1 z_i
-    nd = woodbury.NystromDerivative(op, piv)
+    nd = woodbury.NystromDerivative(op, piv) if dprec is None else dprec
     probeK = np.zeros(p)
     probeP = np.zeros(p)
     trP = np.zeros(p)

@@ -1,0 +1,99 @@
+"""Random Fourier feature preconditioner, FP64 (test infrastructure only).
+
+Tab. 2 of the paper lists random Fourier features (RFF; Prop. "RFF approximation
+quality", after Rahimi and Recht 2007) as a diagonal-plus-low-rank preconditioner
+P_hat = sigma^2 I + Phi Phi^T whose error decays like k^-1/2 with high probability.
+The features are not printed; this is the standard paired form.  By Bochner's theorem a
+stationary kernel is k(x - y) = s E_w[cos(w . (x - y))] with w drawn from its spectral
+density, and cos(a - b) = cos a cos b + sin a sin b, so with m frequencies w_j
+
+    Phi[a, j] = sqrt(s / m) cos(w_j . x_a),   Phi[a, m + j] = sqrt(s / m) sin(w_j . x_a)
+
+(k = 2m features) gives E[Phi Phi^T] = K.  The spectral densities, written as scale
+mixtures of the Gaussian N(0, diag(l)^-2) with w_j = rho_j eps_j / l (elementwise),
+eps_j ~ N(0, I_d):
+    RBF                        rho = 1
+    Matern-nu (nu = 3/2, 5/2)  rho = sqrt(nu / g_j), g_j ~ Gamma(nu, 1)
+                               (a multivariate t with 2 nu degrees of freedom)
+    rational quadratic, alpha = 1   rho = sqrt(g_j), g_j ~ Gamma(1, 1)
+                               (1 / (1 + r^2 / 2) = E_g[exp(-g r^2 / 2)])
+The random draws (eps, g) are inputs, so the oracle and the CUDA path see the same
+frequencies.
+
+The gradient's preconditioner terms need dP_hat/dtheta at frozen draws (the analogue
+of the partial Cholesky's frozen pivots):
+    dPhi/dl_i: with u_j = rho_j eps_j and x~ = x / l, arg = u_j . x~ and
+               d arg / d l_i = -u_ji x~_i / l_i, so d cos = sin u_ji x~_i / l_i and
+               d sin = -cos u_ji x~_i / l_i (an isotropic l sums over i: -arg / l);
+    dPhi/ds  = Phi / (2 s);
+    dP_hat   = dPhi Phi^T + Phi dPhi^T (noise: the identity).
+"""
+import numpy as np
+
+from . import kernels
+
+
+def gamma_shape(kind):
+    """Shape of the Gamma draws g_j the kernel's spectral density needs (None: RBF)."""
+    return {kernels.RBF: None, kernels.MATERN32: 1.5, kernels.MATERN52: 2.5,
+            kernels.RATQUAD: 1.0}[kind]
+
+
+def frequencies(kind, eps, g):
+    """u_j = rho_j eps_j: the frequencies in units of 1 / l (m x d)."""
+    eps = np.asarray(eps, np.float64)
+    if kind == kernels.RBF:
+        rho = np.ones(eps.shape[0])
+    elif kind == kernels.RATQUAD:
+        rho = np.sqrt(np.asarray(g, np.float64))
+    else:
+        rho = np.sqrt(gamma_shape(kind) / np.asarray(g, np.float64))
+    return rho[:, None] * eps
+
+
+class RandomFourier:
+    """Phi (n x 2m) and its derivatives for the hyperparameters theta (the order of
+    ``kernels.kernel_grad_blocks`` followed by the noise)."""
+
+    def __init__(self, kind, X, theta, ard, eps, g):
+        self.X = np.asarray(X, np.float64)
+        self.n, self.d = self.X.shape
+        self.ard = ard
+        self.ls, self.s, self.s2 = kernels.unpack(theta, self.d, ard)
+        self.p = kernels.n_hyper(self.d, ard)
+        self.U = frequencies(kind, eps, g)                      # m x d
+        self.m = self.U.shape[0]
+        self.Xs = self.X / self.ls                              # x~ = x / l
+        arg = self.Xs @ self.U.T                                # n x m
+        self.amp = np.sqrt(self.s / self.m)
+        self.cos, self.sin = np.cos(arg), np.sin(arg)
+        self.arg = arg
+        self.Phi = self.amp * np.hstack([self.cos, self.sin])
+
+    def dphi(self, q):
+        """dPhi / dtheta_q (n x 2m) for q < p - 1."""
+        nls = kernels.n_lengthscales(self.d, self.ard)
+        if q == nls:                                            # output scale
+            return self.Phi / (2.0 * self.s)
+        if self.ard:
+            # d arg / d l_q = -u_jq x~_q / l_q
+            darg = -(self.Xs[:, q][:, None] * self.U[:, q][None, :]) / self.ls[q]
+        else:
+            darg = -self.arg / self.ls[0]
+        return self.amp * np.hstack([-self.sin * darg, self.cos * darg])
+
+    def apply(self, q, V):
+        """dP_hat / dtheta_q @ V."""
+        V = np.asarray(V, np.float64)
+        if q == self.p - 1:
+            return V.copy()
+        dP = self.dphi(q)
+        return dP @ (self.Phi.T @ V) + self.Phi @ (dP.T @ V)
+
+    def diag(self, q):
+        if q == self.p - 1:
+            return np.ones(self.n)
+        return 2.0 * np.sum(self.dphi(q) * self.Phi, axis=1)
+
+    def dense(self, q):
+        return self.apply(q, np.eye(self.n))
