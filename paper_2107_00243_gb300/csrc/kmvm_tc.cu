@@ -14,8 +14,9 @@
 //          (~24 bits): on inputs with large norms (|x|^2 ~ 30) the 16-bit form
 //          perturbs K by |dK|_2 ~ 1e-6 n, which exceeds sigma^2 = 0.1 at n = 5e5.
 //   epilogue  P = k(S) / s in [0, 1], FP32 in registers, rounded to FP16 (11
-//          significant bits) and written back over the same TMEM columns;
-//          tcgen05.ld / tcgen05.st, one thread per row.
+//          significant bits) and written to one of two 64-column TMEM P buffers (two
+//          FP16 values per column), so the S buffer is free for the next GEMM1 as soon
+//          as it has been read; tcgen05.ld / tcgen05.st, one thread per row.
 //   GEMM2  O_I += P [V_hi | V_lo]   (A = P from TMEM, B = the FP16 hi and lo parts of
 //          the V tile in shared memory, N = 2 tp).  Each column c of V is scaled by a
 //          power of two 2^e_c that puts max |V_c| in [2^13, 2^14), so both parts stay
@@ -429,8 +430,43 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
         const uint32_t fb = split ? 1u - sbuf : sbuf;
         const bool wait_p = (split && team == 1) || k >= 1;
         const uint32_t p_par = (split && team == 1) ? (k & 1u) : ((k - 1u) & 1u);
+        if (!split) {
+          // fast mode: both 32-column chunks are loaded first, so the S buffer goes back
+          // to GEMM1 before any exponential, and one store wait covers both chunks
+          uint32_t v0[32], v1[32];
+          GP_TMEM_LD32(tmem + sbuf * 128 + lane_off + half * 64, v0);
+          GP_TMEM_LD32(tmem + sbuf * 128 + lane_off + half * 64 + 32, v1);
+          tmem_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars->s_free[sbuf]));
+          if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
+            for (int q = 0; q < 32; ++q) {
+              g.dbg[row * BN + half * 64 + q] = __uint_as_float(v0[q]);
+              g.dbg[row * BN + half * 64 + 32 + q] = __uint_as_float(v1[q]);
+            }
+          }
+          uint32_t pk0[16], pk1[16];
+          if (g.kind == GP_RBF) p_from_s<GP_RBF>(v0, pk0, pk0, false);
+          else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v0, pk0, pk0, false);
+          else if (g.kind == GP_RATQUAD) p_from_s<GP_RATQUAD>(v0, pk0, pk0, false);
+          else p_from_s<GP_MATERN52>(v0, pk0, pk0, false);
+          if (wait_p && !mbar_wait(smem_u32(&bars->p_free[fb]), p_par, abort, g.err, 33)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          GP_TMEM_ST16(tmem + 256 + pb * 64 + lane_off + half * 32, pk0);
+          if (g.kind == GP_RBF) p_from_s<GP_RBF>(v1, pk1, pk1, false);
+          else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v1, pk1, pk1, false);
+          else if (g.kind == GP_RATQUAD) p_from_s<GP_RATQUAD>(v1, pk1, pk1, false);
+          else p_from_s<GP_MATERN52>(v1, pk1, pk1, false);
+          GP_TMEM_ST16(tmem + 256 + pb * 64 + lane_off + half * 32 + 16, pk1);
+          // tcgen05.st reads its source registers asynchronously
+          tmem_wait_st();
+        }
 #pragma unroll 1
-        for (int c = 0; c < 2 && ok; ++c) {
+        for (int c = 0; c < 2 && ok && split; ++c) {
           const int col0 = half * 64 + c * 32;
           uint32_t v[32];
           GP_TMEM_LD32(tmem + sbuf * 128 + lane_off + col0, v);
