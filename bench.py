@@ -334,15 +334,45 @@ def run_case(args):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
     else:
+        # 20 CG iterations (the tolerance is out of reach, so every column runs them all);
+        # phase 0 times the products, phase 2 the rest of each iteration
         L, piv, rank = gp.gp_pivchol(prob, p.k)
-        o = gp.opts(cg_tol=p.tol, max_iter=4, recompute_every=p.recompute_every, seed=0)
+        its = 20
+        o = gp.opts(cg_tol=1e-12, max_iter=its, recompute_every=0, seed=0)
+        gp.mvm_timing(True)
+        side = []
         for _ in range(args.reps):
+            gp.phase_timing_read(0)
+            gp.phase_timing_read(2)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             gp.gp_mbcg(prob, L, V, o)
             e1.record()
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
+            prod_ms, prod_n = gp.phase_timing_read(0)
+            side_ms, side_n = gp.phase_timing_read(2)
+            side.append({"products_ms": prod_ms, "products": prod_n, "cg_side_ms": side_ms,
+                         "iterations": side_n // 2,
+                         # the whole call less its products, per iteration (includes the
+                         # set-up and the first preconditioner solve)
+                         "call_less_products_ms_per_iteration": (times[-1] - prod_ms) / its})
+        gp.mvm_timing(False)
+        per = [x["cg_side_ms"] / max(x["iterations"], 1) for x in side[1:] or side]
+        best = min(per) if min(per) > 0 else float("nan")
+        esz = 4 if prec != gp.FP64 else 8
+        # algorithmic bytes of one iteration's CG side: L streamed twice, and the n x t
+        # vectors: P, Q (alpha); X, P, Q, R read and X, R written (update); R (L^T R);
+        # R read, Z written (z); P, Z read and P written (direction)
+        traffic = (2 * p.n * p.k + 14 * p.n * t) * esz
+        fmas = 2 * p.n * p.k * t
+        print(json.dumps({"case": "cg_side", "n": p.n, "k": p.k, "t": t,
+                          "precision": args.precision, "ms_per_iteration": best,
+                          "ms_per_iteration_all": per, "algorithmic_bytes": traffic,
+                          "achieved_gbs": traffic / (best * 1e-3) / 1e9,
+                          "fma_per_iteration": fmas,
+                          "achieved_fp32_tflops": 2 * fmas / (best * 1e-3) / 1e12,
+                          "calls": side}), flush=True)
     print(json.dumps({"case": args.case, "n": p.n, "t": t, "precision": args.precision,
                       "ms": times}), flush=True)
 
@@ -488,8 +518,13 @@ def run_synthetic(args):
     names = {workloads.RBF: "RBF", workloads.MATERN32: "Matern32", workloads.RATQUAD: "RatQuad"}
     seeds = args.reps if args.reps and args.reps > 3 else 25
     rows = []
+    only = None
+    if args.rows:
+        only = {tuple(int(v) for v in r.split(":")) for r in args.rows.split(",")}
     for kind in (workloads.MATERN32, workloads.RBF, workloads.RATQUAD):
         for d in (1, 2, 3):
+            if only is not None and (kind, d) not in only:
+                continue
             p = workloads.synthetic_study(kind, d)
             ex = exact[f"{kind}_{d}"]
             ref = np.array([ex["mll"]] + ex["grad"])
@@ -522,10 +557,79 @@ def run_synthetic(args):
     print("|---|---|---|---|---|---|---|---|---|---|---|---|")
     for r in rows:
         b, v = r["bias"], r["var"]
-        print(f"| {r['kernel']} | {r['d']} | {r['k']} ({r['rank']}) | {b['mll']:.0e} | {v['mll']:.0e} | "
+        print(f"| {r['kernel']} | {r['d']} | {r['k']} ({r['rank']}) | {b['mll']:.0e} | "
+              f"{v['mll']:.0e} | "
               f"{b['outputscale']:.0e} | {v['outputscale']:.0e} | {b['lengthscale']:.0e} | "
               f"{v['lengthscale']:.0e} | {b['noise']:.0e} | {v['noise']:.0e} | "
               f"{r['cg_iters_max']} |")
+
+
+def run_decay(args):
+    """The residual-decay experiment (Fig. 2; rates of Tab. 2): as the rank k of the partial
+    Cholesky preconditioner (or the number of random Fourier features, mean over four
+    draws) grows, log det P_hat_k -> log det K_hat and tr(P_hat_k^-1 dP_hat_k) ->
+    tr(K_hat^-1 dK_hat) for every hyperparameter, at the rate at which P_hat_k -> K_hat
+    (the residual trace tr(K - L L^T) / tr K).  Four n = 1,000 problems of the synthetic
+    study's generator (RBF and Matern-3/2, d = 1 and 3), FP64; the exact values are
+    tests/golden/residual_decay_exact.json (dense Cholesky, FP64 oracle).  Prints one
+    JSON line per (problem, k) and a markdown table."""
+    import torch
+    from paper_2107_00243_gb300 import build, gp, workloads
+    build.build()
+    gp.load()
+    with open(os.path.join(ROOT, "tests", "golden", "residual_decay_exact.json")) as f:
+        gold = json.load(f)
+    names = {workloads.RBF: "RBF", workloads.MATERN32: "Matern32"}
+    ks = [0, 1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256]
+    rows = []
+    for key, ex in gold["problems"].items():
+        kind, d = (int(v) for v in key.split("_"))
+        p = workloads.synthetic_study(kind, d, n=gold["n"])
+        prob = gp.Problem(p.X, p.theta, p.kind, p.ard, gp.FP64)
+        o = gp.opts(cg_tol=1e-10, max_iter=1, seed=0)      # CG is not needed here
+        trK = p.n * p.theta[-2]                            # noise-free tr K
+        for k in ks:
+            st, out, iout = gp.gp_mll_and_grad(prob, p.y, k, 1, o)
+            r = gp.unpack(out, iout, prob.p, 1, k)
+            res = 1.0
+            if k > 0:
+                L, _, _ = gp.gp_pivchol(prob, k)
+                res = max(trK - float((L.double() ** 2).sum()), 0.0) / trK
+            e_ld = abs(r["logdetP"] - ex["logdet"]) / abs(ex["logdet"])
+            tp = [float(v) for v in ex["trace_p"]]
+            e_tr = [abs(float(a) - b) / abs(b) for a, b in zip(r["trP_p"], tp)]
+            row = {"kernel": names[kind], "d": d, "n": p.n, "preconditioner": "cholesky",
+                   "k": k, "rank": r["rank"], "residual_trace": res, "logdet_rel_err": e_ld,
+                   "trace_rel_err": {"lengthscale": e_tr[0], "outputscale": e_tr[1],
+                                     "noise": e_tr[2]}}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        # random Fourier features (Tab. 2: error ~ k^-1/2), the mean over four draws
+        for k in (16, 64, 256, 1000):
+            m = k // 2
+            acc = [0.0, 0.0, 0.0, 0.0]
+            for draw in range(4):
+                eps, g = workloads.rff_draws(m, d, gp.rff_gamma_shape(kind), seed=draw)
+                st, out, iout = gp.gp_mll_and_grad_rff(prob, p.y, m, 1, o, eps, g)
+                r = gp.unpack(out, iout, prob.p, 1, k)
+                acc[0] += abs(r["logdetP"] - ex["logdet"]) / abs(ex["logdet"]) / 4
+                for q in range(3):
+                    acc[1 + q] += abs(float(r["trP_p"][q]) - float(ex["trace_p"][q])) / abs(
+                        float(ex["trace_p"][q])) / 4
+            row = {"kernel": names[kind], "d": d, "n": p.n, "preconditioner": "rff", "k": k,
+                   "rank": k, "residual_trace": float("nan"), "logdet_rel_err": acc[0],
+                   "trace_rel_err": {"lengthscale": acc[1], "outputscale": acc[2],
+                                     "noise": acc[3]}, "draws": 4}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    print("| kernel | d | preconditioner | k (rank) | tr(K - LL^T) / tr K | log det rel. err | "
+          "tr d/dl rel. err | tr d/ds rel. err | tr d/dsigma2 rel. err |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    for r in rows:
+        t = r["trace_rel_err"]
+        print(f"| {r['kernel']} | {r['d']} | {r['preconditioner']} | {r['k']} ({r['rank']}) | "
+              f"{r['residual_trace']:.1e} | {r['logdet_rel_err']:.1e} | {t['lengthscale']:.1e} | "
+              f"{t['outputscale']:.1e} | {t['noise']:.1e} |")
 
 
 def main():
@@ -538,8 +642,10 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=1,
                     help="timed steps of the plain FP32 form when --precision is mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", default="",
+                    help="synthetic: only these kernel:d problems, e.g. 7:2,7:3")
     ap.add_argument("--case", choices=["estimator", "kmvm", "mbcg", "grad", "batched", "peaks",
-                                       "c4", "synthetic"],
+                                       "c4", "synthetic", "decay"],
                     default="estimator",
                     help="kmvm / mbcg / grad: time only the kernel product, a short CG call "
                          "or the gradient contraction on an instance of the workload (for "
@@ -555,6 +661,9 @@ def main():
         return
     if args.case == "c4":
         run_c4(args)
+        return
+    if args.case == "decay":
+        run_decay(args)
         return
     if args.case == "synthetic":
         run_synthetic(args)

@@ -234,6 +234,26 @@ gp_status gp_mll_and_grad(const gp_problem* prob, const void* y, int32_t k,
                           double* out, int32_t* iout, const gp_opts* opts, void* ws,
                           size_t ws_bytes, gp_stream_t stream);
 
+/* The same estimator with a random Fourier feature preconditioner in place of the
+ * partial Cholesky factor (Tab. 2 "RFF"; Prop. "RFF approximation quality", after
+ * Rahimi and Recht 2007): P_hat = sigma^2 I + Phi Phi^T with k = 2m features
+ *   Phi[a, j] = sqrt(s/m) cos(u_j . x~_a),  Phi[a, m + j] = sqrt(s/m) sin(u_j . x~_a),
+ * x~ = (x - mean x) / l (elementwise for ARD; the inputs' mean as the origin, which
+ * leaves P_hat unchanged and fixes the probes), u_j = rho_j eps_j drawn from the
+ * kernel's spectral density: RBF rho = 1; Matern-3/2 and -5/2 rho = sqrt(nu / g_j) with g_j ~ Gamma(nu, 1);
+ * rational quadratic (alpha = 1) rho = sqrt(g_j) with g_j ~ Gamma(1, 1).
+ * eps: device, m x d doubles (row-major), standard-normal draws; g: device, m doubles
+ * (may be NULL for the RBF).  The gradient's preconditioner terms take dP_hat at these
+ * frozen draws.  Everything else (probes with k = 2m, mBCG, quadrature, contraction,
+ * outputs, iout with rank = 2m and pivots -1, statuses, synchronisation) is as for
+ * gp_mll_and_grad with k = 2m; the workspace is gp_workspace_size(GP_FN_MLL_AND_GRAD,
+ * n, d, 2m, n_probes + 1, ...).  Requires 1 <= m and 2m <= min(n, the largest k).     */
+gp_status gp_mll_and_grad_rff(const gp_problem* prob, const void* y, int32_t m,
+                              int32_t n_probes, const double* eps, const double* g,
+                              const int8_t* eps_override, const int32_t* iters_override,
+                              double* out, int32_t* iout, const gp_opts* opts, void* ws,
+                              size_t ws_bytes, gp_stream_t stream);
+
 /* Batched estimator: n_problems independent problems (each its own n, d, X,
  * hyperparameters and precision; shared k, n_probes and opts; problem i draws its
  * probes from seed opts->seed + i).  The per-probe loops of Alg. 1 and Alg. 2 are
@@ -326,10 +346,12 @@ gp_status gp_tc_exponent_tile(const gp_problem* prob, const void* V, int64_t ldv
 int64_t gp_launch_count(void);
 void gp_mvm_timing(int32_t enable);
 gp_status gp_mvm_timing_read(double* total_ms, int64_t* products);
-/* The same timing for a phase of gp_mll_and_grad: phase 0 = the kernel-matrix
- * products (as gp_mvm_timing_read), phase 1 = the gradient contraction of Alg. 2
- * (one bracket per evaluation).  Returns (and resets) the summed duration in ms and
- * the number of brackets.                                                         */
+/* The same timing for a phase of gp_mll_and_grad / gp_mbcg: phase 0 = the
+ * kernel-matrix products (as gp_mvm_timing_read), phase 1 = the gradient contraction
+ * of Alg. 2 (one bracket per evaluation), phase 2 = the work of a CG iteration outside
+ * its products (two brackets per iteration: the alpha / update step, then the
+ * preconditioner solve and the direction update; eager calls only).  Returns (and
+ * resets) the summed duration in ms and the number of brackets.                    */
 gp_status gp_phase_timing_read(int32_t phase, double* total_ms, int64_t* count);
 
 /* Throughput microbenchmarks of the arithmetic units the path uses (roofline

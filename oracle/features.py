@@ -18,11 +18,14 @@ eps_j ~ N(0, I_d):
     rational quadratic, alpha = 1   rho = sqrt(g_j), g_j ~ Gamma(1, 1)
                                (1 / (1 + r^2 / 2) = E_g[exp(-g r^2 / 2)])
 The random draws (eps, g) are inputs, so the oracle and the CUDA path see the same
-frequencies.
+frequencies.  The paper fixes no origin for x: shifting every x by c turns each
+(cos, sin) pair by the angle u_j . c, which leaves Phi Phi^T (so P_hat) unchanged but
+changes the probes Phi eps_1.  The features are taken at x~ = (x - mean x) / l, the
+inputs' own mean as the origin (the CUDA path centres its inputs the same way).
 
 The gradient's preconditioner terms need dP_hat/dtheta at frozen draws (the analogue
 of the partial Cholesky's frozen pivots):
-    dPhi/dl_i: with u_j = rho_j eps_j and x~ = x / l, arg = u_j . x~ and
+    dPhi/dl_i: with u_j = rho_j eps_j and x~ = (x - mean x) / l, arg = u_j . x~ and
                d arg / d l_i = -u_ji x~_i / l_i, so d cos = sin u_ji x~_i / l_i and
                d sin = -cos u_ji x~_i / l_i (an isotropic l sums over i: -arg / l);
     dPhi/ds  = Phi / (2 s);
@@ -63,7 +66,9 @@ class RandomFourier:
         self.p = kernels.n_hyper(self.d, ard)
         self.U = frequencies(kind, eps, g)                      # m x d
         self.m = self.U.shape[0]
-        self.Xs = self.X / self.ls                              # x~ = x / l
+        # x~ = (x - mean x) / l: the origin of the features is the input mean (any fixed
+        # shift rotates each cos / sin pair and leaves Phi Phi^T unchanged)
+        self.Xs = (self.X - self.X.mean(axis=0)) / self.ls
         arg = self.Xs @ self.U.T                                # n x m
         self.amp = np.sqrt(self.s / self.m)
         self.cos, self.sin = np.cos(arg), np.sin(arg)

@@ -408,6 +408,7 @@ struct MllPlan {
   T* L;
   int* pivots;
   int* rank;
+  double* featU;     // random Fourier features: m x d frequencies (m <= k / 2)
   T* B;
   T* PinvB;
   double* wts;
@@ -423,6 +424,7 @@ void plan_mll(Arena& A, const Prob& pb, int k, int nl, int max_iter, MllPlan<T>&
   plan_core(A, pb, k, P.core);
   plan_cg<T>(A, pb, k, t, max_iter, P.cg);
   plan_prec(A, pb, k, nl, P.prec);
+  P.featU = A.take<double>((size_t)std::max(k / 2, 1) * pb.d);
   P.use_tg = P.mvm.use_tc && tc_grad_supported(pb, t);
   P.tg = TcGradBufs{};
   if (P.use_tg) {
@@ -450,7 +452,7 @@ template <class T>
 gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
                    const int* piv_override, const int* iters_override, double* out, int* iout,
                    const gp_opts& o, void* ws, size_t ws_bytes, cudaStream_t st,
-                   int side_index = 0) {
+                   int side_index = 0, const FeatSpec* feat = nullptr) {
   const int t = nl + 1;
   MllPlan<T> P;
   {
@@ -474,9 +476,17 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   // S1: scaled inputs
   GP_TRY(run_prep<T>(pb, P.mvm.prep, st));
   const void* Xs = P.mvm.prep.pr.Xs;
-  // S2: pivoted Cholesky
-  GP_TRY(pivchol_run<T>(pb, Xs, k, o.pivchol_tol, piv_override, P.L, pb.n, P.pivots, P.rank,
-                        P.piv.b, st));
+  if (feat) {
+    // S2': random Fourier features (Tab. 2) as the low-rank factor: rank k = 2m, no pivots
+    GP_TRY(rff_build<T>(pb, Xs, feat->m, feat->eps, feat->g, P.featU, P.L, pb.n, st));
+    GP_CUDA_TRY(cudaMemsetAsync(P.pivots, 0xff, sizeof(int) * (size_t)k, st));
+    set_int_kernel<<<1, 1, 0, st>>>(P.rank, k);
+    GP_LAUNCH_CHECK();
+  } else {
+    // S2: pivoted Cholesky
+    GP_TRY(pivchol_run<T>(pb, Xs, k, o.pivchol_tol, piv_override, P.L, pb.n, P.pivots, P.rank,
+                          P.piv.b, st));
+  }
   // S3: Woodbury core and log det P_hat
   if (k > 0) GP_TRY(atb<T>(pb.n, P.L, pb.n, k, P.L, pb.n, k, P.core.atb_part, P.core.G, st));
   GP_TRY(woodbury_core(k, P.core.G, pb.theta, pb.D, pb.n, P.core.Cfac, P.core.Cinv, P.core.work,
@@ -543,9 +553,15 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   }
   if (timed) mvm_timing_end(st, 1);
   // S10: preconditioner terms with W = P^-1 z_i (columns 1..l of PinvB)
-  GP_TRY(precond_terms<T>(pb, Xs, P.L, pb.n, k, P.pivots, P.rank, P.PinvB + pb.n, pb.n, nl,
-                          P.core.Cinv, P.prec, out + GP_OUT_TRP(pb.p), out + GP_OUT_PROBEP(pb.p),
-                          st));
+  if (feat) {
+    GP_TRY(feature_terms<T>(pb, Xs, P.L, pb.n, feat->m, P.featU, P.PinvB + pb.n, pb.n, nl,
+                            P.core.Cinv, P.prec, out + GP_OUT_TRP(pb.p),
+                            out + GP_OUT_PROBEP(pb.p), st));
+  } else {
+    GP_TRY(precond_terms<T>(pb, Xs, P.L, pb.n, k, P.pivots, P.rank, P.PinvB + pb.n, pb.n, nl,
+                            P.core.Cinv, P.prec, out + GP_OUT_TRP(pb.p),
+                            out + GP_OUT_PROBEP(pb.p), st));
+  }
   // S11: assembly
   GP_CUDA_TRY(cudaStreamWaitEvent(st, side.join, 0));
   assemble<<<1, 32, 0, st>>>(pb.n, pb.p, nl, k, P.rank, P.cg.iters, P.pivots, P.cg.status,
@@ -610,7 +626,7 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
         gp_opts o2 = o;
         o2.flags |= GP_OPT_SPLIT_P;
         r = mll_impl<T>(pb, y, k, nl, eps, piv_override, iters_override, out, iout, o2, ws,
-                        ws_bytes, st, side_index);
+                        ws_bytes, st, side_index, feat);
         if (r < 0) return r;
       }
       // report the estimates in the output head (GP_OUT_DRIFT_QUAD / _LOGDET)
@@ -974,6 +990,35 @@ extern "C" gp_status gp_mll_and_grad(const gp_problem* prob, const void* y, int3
                          iters_override, out, iout, *opts, ws, ws_bytes, st);
 }
 
+extern "C" gp_status gp_mll_and_grad_rff(const gp_problem* prob, const void* y, int32_t m,
+                                         int32_t n_probes, const double* eps, const double* g,
+                                         const int8_t* eps_override,
+                                         const int32_t* iters_override, double* out,
+                                         int32_t* iout, const gp_opts* opts, void* ws,
+                                         size_t ws_bytes, gp_stream_t stream) {
+  GP_TRY(check_problem(prob));
+  GP_TRY(check_opts(opts));
+  GP_REQUIRE(y && out && iout, "y, out or iout is NULL");
+  GP_REQUIRE(m >= 1 && 2 * (int64_t)m <= kMaxK && 2 * (int64_t)m <= prob->n,
+             "m=%d out of range [1, min(n, %d) / 2]", m, kMaxK);
+  GP_REQUIRE(eps, "eps is NULL");
+  GP_REQUIRE(g || prob->kind == GP_RBF, "g is NULL (every kernel but the RBF needs it)");
+  GP_REQUIRE(n_probes >= 0 && n_probes + 1 <= kMaxT, "n_probes=%d out of range", n_probes);
+  Prob pb = make_prob(prob);
+  const int t = n_probes + 1, k = 2 * m;
+  GP_REQUIRE(!((pb.prec == GP_BF16 || pb.prec == GP_TF32) && !tc_supported(pb, t)),
+             "tensor-core precision does not support this shape");
+  GP_TRY(check_ws(ws, ws_bytes,
+                  gp_workspace_size(GP_FN_MLL_AND_GRAD, pb.n, pb.d, k, t, pb.prec, opts->max_iter)));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const FeatSpec feat{m, eps, g};
+  if (pb.prec == GP_FP64)
+    return mll_impl<double>(pb, (const double*)y, k, n_probes, eps_override, nullptr,
+                            iters_override, out, iout, *opts, ws, ws_bytes, st, 0, &feat);
+  return mll_impl<float>(pb, (const float*)y, k, n_probes, eps_override, nullptr,
+                         iters_override, out, iout, *opts, ws, ws_bytes, st, 0, &feat);
+}
+
 // ---- batched evaluation --------------------------------------------------------------
 // Independent problems run concurrently on a pool of worker streams (each problem's
 // own steps stay in order on one stream; its Lanczos quadrature forks to a side
@@ -1208,8 +1253,8 @@ std::atomic<long long> g_launches{0};
 std::atomic<int> g_timing{0};
 std::mutex g_tmu;
 std::vector<cudaEvent_t> g_free_events;
-std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_pairs[2];   // per phase
-cudaEvent_t g_open[2] = {nullptr, nullptr};
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_pairs[3];   // per phase
+cudaEvent_t g_open[3] = {nullptr, nullptr, nullptr};
 cudaEvent_t take_event() {
   if (!g_free_events.empty()) {
     cudaEvent_t e = g_free_events.back();
@@ -1267,7 +1312,7 @@ extern "C" gp_status gp_mvm_timing_read(double* total_ms, int64_t* products) {
 }
 
 extern "C" gp_status gp_phase_timing_read(int32_t phase, double* total_ms, int64_t* count) {
-  GP_REQUIRE(phase == 0 || phase == 1, "phase must be 0 or 1");
+  GP_REQUIRE(phase >= 0 && phase <= 2, "phase must be 0, 1 or 2");
   return gp::phase_timing_read(phase, total_ms, count);
 }
 

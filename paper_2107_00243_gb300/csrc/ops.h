@@ -199,6 +199,23 @@ struct PrecBufs {
   double* part;     // 2 n k reals in the problem precision: Z1 = L A1^T, Z2 = W Cv^T
   double* dkpart;   // max(atb partials of L^T W, per-block E / F partials)
 };
+// Random Fourier feature preconditioner: m frequencies u_j = rho_j eps_j (U, m x d FP64)
+// from the standard-normal draws eps (m x d, row-major) and the Gamma draws g (m; unused
+// for the RBF), and the n x 2m feature matrix Phi (ld ldp) in the problem precision.
+struct FeatSpec {
+  int m;
+  const double* eps;
+  const double* g;
+};
+template <class T>
+gp_status rff_build(const Prob& pb, const void* Xs, int m, const double* eps, const double* g,
+                    double* U, T* Phi, int64_t ldp, cudaStream_t st);
+// trP and probeP of P_hat = sigma^2 I + Phi Phi^T (dP_hat at frozen draws).
+template <class T>
+gp_status feature_terms(const Prob& pb, const void* Xs, const T* Phi, int64_t ldp, int m,
+                        const double* U, const T* W, int64_t ldw, int n_probes,
+                        const double* Cinv, const PrecBufs& b, double* trP, double* probeP,
+                        cudaStream_t st);
 template <class T>
 gp_status precond_terms(const Prob& pb, const void* Xs, const T* L, int64_t ldl, int k,
                         const int* piv, const int* rank, const T* W, int64_t ldw, int n_probes,

@@ -251,7 +251,8 @@ __global__ void __launch_bounds__(256) terms_kernel(
     int k, int nl, int P, int64_t n, const double* __restrict__ theta, int D, int NQ, int DM,
     const double* __restrict__ EF, const double* __restrict__ dW, const double* __restrict__ B1,
     const double* __restrict__ Cv, const double* __restrict__ Cinv,
-    const double* __restrict__ wnorm2, double* __restrict__ trP, double* __restrict__ probeP) {
+    const double* __restrict__ wnorm2, double* __restrict__ trP, double* __restrict__ probeP,
+    int nystrom) {
   __shared__ double sh[32];
   const int q = blockIdx.x;
   const double s2 = theta[D + 1];
@@ -266,6 +267,14 @@ __global__ void __launch_bounds__(256) terms_kernel(
     return;
   }
   const int slot = (q == D) ? DM : q;          // E/F index of this hyperparameter
+  if (!nystrom) {
+    // features: dP_hat = dPhi Phi^T + Phi dPhi^T has no pivot-block term
+    if (threadIdx.x == 0) {
+      trP[q] = 2.0 * EF[slot];
+      probeP[q] = nl > 0 ? 2.0 * EF[NQ + slot] / nl : 0.0;
+    }
+    return;
+  }
   const double* dWq = dW + (int64_t)q * k * k;
   double t2 = 0.0;
   for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) t2 += B1[e] * dWq[e];
@@ -305,6 +314,138 @@ __global__ void sumsq_kernel(int64_t n, int nl, const T* __restrict__ W, int64_t
       for (unsigned b = 0; b < gridDim.x; ++b) r += part[b];
       *out = r;
     }
+  }
+}
+
+// ---- random Fourier feature preconditioner (Tab. 2 "RFF") -----------------------------
+// P_hat = sigma^2 I + Phi Phi^T with m frequencies u_j (in units of 1 / l) and k = 2m
+// features  Phi[a, j] = sqrt(s/m) cos(u_j . x~_a),  Phi[a, m + j] = sqrt(s/m) sin(u_j . x~_a)
+// (x~ = (x - mean x) / l, the centred inputs of S1: a shift of the origin only turns each
+// cos / sin pair, so Phi Phi^T is the same).  By Bochner's theorem E[Phi Phi^T] = K when
+// u_j is drawn from the kernel's spectral density, written as a Gaussian scale mixture
+// u_j = rho_j eps_j:
+//   RBF rho = 1;  Matern-nu rho = sqrt(nu / g_j), g_j ~ Gamma(nu, 1) (a multivariate t
+//   with 2 nu degrees of freedom);  rational quadratic (alpha = 1) rho = sqrt(g_j),
+//   g_j ~ Gamma(1, 1) (1 / (1 + r^2/2) = E_g[exp(-g r^2 / 2)]).
+// The draws eps_j, g_j are inputs.  Arguments and features are formed in FP64 (one pass
+// each per evaluation) and stored in the problem precision.
+constexpr int kFeatChunk = 32;    // frequencies staged in shared memory per step
+
+__global__ void rff_freq_kernel(int kind, int m, int d, const double* __restrict__ eps,
+                                const double* __restrict__ g, double* __restrict__ U) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * d) return;
+  const int j = e / d;
+  double rho = 1.0;
+  if (kind == GP_RATQUAD) rho = sqrt(g[j]);
+  else if (kind == GP_MATERN32) rho = sqrt(1.5 / g[j]);
+  else if (kind == GP_MATERN52) rho = sqrt(2.5 / g[j]);
+  U[e] = rho * eps[e];
+}
+
+// One thread per row a, a chunk of kFeatChunk frequencies per block (grid.y).
+template <class T, int DM>
+__global__ void __launch_bounds__(256) rff_build_kernel(int64_t n, int d, int m,
+                                                        const T* __restrict__ Xs,
+                                                        const double* __restrict__ U,
+                                                        const double* __restrict__ theta, int D,
+                                                        T* __restrict__ Phi, int64_t ldp) {
+  __shared__ double su[kFeatChunk][DM];
+  const int j0 = blockIdx.y * kFeatChunk;
+  const int jn = min(kFeatChunk, m - j0);
+  for (int e = threadIdx.x; e < kFeatChunk * DM; e += blockDim.x) {
+    const int jj = e / DM, u = e % DM;
+    su[jj][u] = (jj < jn && u < d) ? U[(int64_t)(j0 + jj) * d + u] : 0.0;
+  }
+  __syncthreads();
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  double xa[DM];
+#pragma unroll
+  for (int u = 0; u < DM; ++u) xa[u] = u < d ? (double)Xs[a * d + u] : 0.0;
+  const double amp = sqrt(theta[D] / m);
+  for (int jj = 0; jj < jn; ++jj) {
+    double arg = 0.0;
+#pragma unroll
+    for (int u = 0; u < DM; ++u) arg = fma(su[jj][u], xa[u], arg);
+    double sn, c;
+    sincos(arg, &sn, &c);
+    Phi[a + (int64_t)(j0 + jj) * ldp] = (T)(amp * c);
+    Phi[a + (int64_t)(m + j0 + jj) * ldp] = (T)(amp * sn);
+  }
+}
+
+// E[q] = sum_{a, j} dPhi_q[a, j] Z1[a, j],  F[q] = sum_{a, j} dPhi_q[a, j] Z2[a, j] over the
+// 2m feature columns, for every lengthscale and the output scale (frozen draws):
+//   d cos / d l_i =  sin(arg) u_ji x~_i / l_i,  d sin / d l_i = -cos(arg) u_ji x~_i / l_i
+//   (an isotropic l: the sum over i, i.e. arg / l),   d Phi / d s = Phi / (2 s).
+// One thread per row a; per-block FP64 partials, as in dk_contract.
+template <class T, int DM>
+__global__ void __launch_bounds__(256) rff_contract(int64_t n, int d, int ard, int D, int m,
+                                                    const double* __restrict__ theta,
+                                                    const T* __restrict__ Xs,
+                                                    const double* __restrict__ U,
+                                                    const T* __restrict__ Z1,
+                                                    const T* __restrict__ Z2,
+                                                    double* __restrict__ part) {
+  constexpr int NQ = DM + 1;
+  __shared__ double su[kFeatChunk][DM];
+  __shared__ double sred[8][2 * NQ];
+  const int64_t a = blockIdx.x * (int64_t)256 + threadIdx.x;
+  double xa[DM];
+#pragma unroll
+  for (int u = 0; u < DM; ++u) xa[u] = (a < n && u < d) ? (double)Xs[a * d + u] : 0.0;
+  const double amp = sqrt(theta[D] / m);
+  double e1[NQ], e2[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { e1[q] = 0.0; e2[q] = 0.0; }
+  for (int j0 = 0; j0 < m; j0 += kFeatChunk) {
+    const int jn = min(kFeatChunk, m - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kFeatChunk * DM; e += 256) {
+      const int jj = e / DM, u = e % DM;
+      su[jj][u] = (jj < jn && u < d) ? U[(int64_t)(j0 + jj) * d + u] : 0.0;
+    }
+    __syncthreads();
+    if (a >= n) continue;
+    for (int jj = 0; jj < jn; ++jj) {
+      const int j = j0 + jj;
+      double arg = 0.0;
+#pragma unroll
+      for (int u = 0; u < DM; ++u) arg = fma(su[jj][u], xa[u], arg);
+      double sn, c;
+      sincos(arg, &sn, &c);
+      const double z1c = (double)Z1[a + (int64_t)j * n], z1s = (double)Z1[a + (int64_t)(m + j) * n];
+      const double z2c = (double)Z2[a + (int64_t)j * n], z2s = (double)Z2[a + (int64_t)(m + j) * n];
+      const double g1 = amp * (sn * z1c - c * z1s), g2 = amp * (sn * z2c - c * z2s);
+      if (ard) {
+#pragma unroll
+        for (int u = 0; u < DM; ++u) {
+          const double w = su[jj][u] * xa[u];
+          e1[u] = fma(g1, w, e1[u]);
+          e2[u] = fma(g2, w, e2[u]);
+        }
+      } else {
+        e1[0] = fma(g1, arg, e1[0]);
+        e2[0] = fma(g2, arg, e2[0]);
+      }
+      e1[DM] += amp * (c * z1c + sn * z1s);
+      e2[DM] += amp * (c * z2c + sn * z2s);
+    }
+  }
+  // scale to the derivative: lengthscale q: / l_q ; output scale: / (2 s)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double sc = (q == DM) ? 0.5 / theta[D] : (q < D ? 1.0 / theta[q] : 0.0);
+    const double v1 = warp_sum(e1[q] * sc), v2 = warp_sum(e2[q] * sc);
+    if (lane == 0) { sred[warp][q] = v1; sred[warp][NQ + q] = v2; }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * NQ; e += 256) {
+    double acc = 0.0;
+    for (int w = 0; w < 8; ++w) acc += sred[w][e];
+    part[(size_t)blockIdx.x * 2 * NQ + e] = acc;
   }
 }
 
@@ -382,10 +523,102 @@ gp_status precond_terms(const Prob& pb, const void* Xs_, const T* L, int64_t ldl
     GP_LAUNCH_CHECK();
   }
   terms_kernel<<<P, 256, 0, st>>>(k, nl, P, pb.n, pb.theta, pb.D, NQ, DM, EF, b.dW, b.B1, b.Cv,
-                                  Cinv, wn, trP, probeP);
+                                  Cinv, wn, trP, probeP, 1);
   GP_LAUNCH_CHECK();
   return GP_OK;
 }
+
+template <class T>
+gp_status rff_build(const Prob& pb, const void* Xs_, int m, const double* eps, const double* g,
+                    double* U, T* Phi, int64_t ldp, cudaStream_t st) {
+  const T* Xs = static_cast<const T*>(Xs_);
+  rff_freq_kernel<<<(unsigned)cdiv((int64_t)m * pb.d, 256), 256, 0, st>>>(pb.kind, m, pb.d, eps,
+                                                                           g, U);
+  GP_LAUNCH_CHECK();
+  const dim3 grid((unsigned)cdiv(pb.n, 256), (unsigned)cdiv(m, kFeatChunk));
+  switch (dm_of(pb.d)) {
+    case 4: rff_build_kernel<T, 4><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, pb.theta, pb.D,
+                                                         Phi, ldp); break;
+    case 8: rff_build_kernel<T, 8><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, pb.theta, pb.D,
+                                                         Phi, ldp); break;
+    case 16: rff_build_kernel<T, 16><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, pb.theta, pb.D,
+                                                           Phi, ldp); break;
+    default: rff_build_kernel<T, 32><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, pb.theta, pb.D,
+                                                           Phi, ldp); break;
+  }
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
+// The feature preconditioner's terms: trP_q = 2 sum(Z1 o dPhi_q) with Z1 = Phi C^-1 and
+// probeP_q = (2 / l) sum(Z2 o dPhi_q) with Z2 = W (Phi^T W)^T, by the same identities
+// as for the partial Cholesky factor (Phi^T P_hat^-1 = C^-1 Phi^T); the noise entries
+// are the same as there.
+template <class T>
+gp_status feature_terms(const Prob& pb, const void* Xs_, const T* Phi, int64_t ldp, int m,
+                        const double* U, const T* W, int64_t ldw, int nl, const double* Cinv,
+                        const PrecBufs& b, double* trP, double* probeP, cudaStream_t st) {
+  const T* Xs = static_cast<const T*>(Xs_);
+  const int P = pb.p, k = 2 * m;
+  double* wn = b.LtW + (int64_t)k * nl;
+  unsigned* ctr = reinterpret_cast<unsigned*>(wn + 1);
+  double* spart = wn + 2;
+  {
+    int blocks = (int)std::min<int64_t>(cdiv(pb.n, 256), 128);
+    GP_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned), st));
+    sumsq_kernel<T><<<blocks, 256, 0, st>>>(pb.n, nl, W, ldw, spart, ctr, wn);
+    GP_LAUNCH_CHECK();
+  }
+  const int DM = dm_of(pb.d), NQ = DM + 1;
+  double* EF = b.Cv + (size_t)std::max(k, 1) * std::max(nl, 1);   // 2 NQ doubles
+  T* Bt = reinterpret_cast<T*>(b.Q);                 // k x k then l x k, problem precision
+  T* Z1 = reinterpret_cast<T*>(b.part);              // n x k
+  T* Z2 = Z1 + (size_t)pb.n * k;                     // n x k
+  // Z1 = Phi C^-1 (C^-1 is symmetric)
+  transpose_to<T><<<(unsigned)cdiv(k * k, 256), 256, 0, st>>>(k, k, Cinv, Bt);
+  GP_LAUNCH_CHECK();
+  const dim3 gz((unsigned)cdiv(pb.n, 128), (unsigned)cdiv(k, 64));
+  gemm_tall<T><<<gz, 256, 0, st>>>(pb.n, k, k, Phi, ldp, Bt, Z1);
+  GP_LAUNCH_CHECK();
+  if (nl > 0) {
+    GP_TRY(atb<T>(pb.n, Phi, ldp, k, W, ldw, nl, b.dkpart, b.LtW, st));   // Phi^T W
+    T* Bt2 = Bt + (size_t)k * k;
+    transpose_to<T><<<(unsigned)cdiv(k * nl, 256), 256, 0, st>>>(k, nl, b.LtW, Bt2);
+    GP_LAUNCH_CHECK();
+    gemm_tall<T><<<gz, 256, 0, st>>>(pb.n, nl, k, W, ldw, Bt2, Z2);      // W (Phi^T W)^T
+    GP_LAUNCH_CHECK();
+  } else {
+    GP_CUDA_TRY(cudaMemsetAsync(Z2, 0, sizeof(T) * (size_t)pb.n * k, st));
+  }
+  const int nblk = (int)cdiv(pb.n, 256);
+  switch (DM) {
+    case 4: rff_contract<T, 4><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.ard, pb.D, m, pb.theta, Xs, U,
+                                                     Z1, Z2, b.dkpart); break;
+    case 8: rff_contract<T, 8><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.ard, pb.D, m, pb.theta, Xs, U,
+                                                     Z1, Z2, b.dkpart); break;
+    case 16: rff_contract<T, 16><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.ard, pb.D, m, pb.theta, Xs,
+                                                       U, Z1, Z2, b.dkpart); break;
+    default: rff_contract<T, 32><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.ard, pb.D, m, pb.theta, Xs,
+                                                       U, Z1, Z2, b.dkpart); break;
+  }
+  GP_LAUNCH_CHECK();
+  dk_combine<<<1, 128, 0, st>>>(nblk, 2 * NQ, b.dkpart, EF);
+  GP_LAUNCH_CHECK();
+  terms_kernel<<<P, 256, 0, st>>>(k, nl, P, pb.n, pb.theta, pb.D, NQ, DM, EF, b.dW, b.B1, b.Cv,
+                                  Cinv, wn, trP, probeP, 0);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
+#define GP_FEAT_INST(T)                                                                        \
+  template gp_status rff_build<T>(const Prob&, const void*, int, const double*, const double*, \
+                                  double*, T*, int64_t, cudaStream_t);                         \
+  template gp_status feature_terms<T>(const Prob&, const void*, const T*, int64_t, int,        \
+                                      const double*, const T*, int64_t, int, const double*,    \
+                                      const PrecBufs&, double*, double*, cudaStream_t);
+GP_FEAT_INST(float)
+GP_FEAT_INST(double)
+#undef GP_FEAT_INST
 
 template gp_status precond_terms<float>(const Prob&, const void*, const float*, int64_t, int,
                                         const int*, const int*, const float*, int64_t, int,

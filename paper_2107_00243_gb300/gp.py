@@ -77,6 +77,8 @@ def load():
         "gp_mbcg": (i32, [P, vp, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp,
                           O, vp, sz, vp]),
         "gp_mll_and_grad": (i32, [P, vp, i32, i32, vp, vp, vp, vp, vp, O, vp, sz, vp]),
+        "gp_mll_and_grad_rff": (i32, [P, vp, i32, i32, vp, vp, vp, vp, vp, vp, O, vp, sz,
+                                      vp]),
         "gp_status_string": (ctypes.c_char_p, [i32]),
         "gp_last_error_message": (ctypes.c_char_p, []),
         "gp_rademacher": (i32, [ctypes.c_uint64, i32, i64, i32, vp, vp]),
@@ -359,6 +361,55 @@ def gp_mll_and_grad(prob, y, k, n_probes, o, eps_override=None, piv_override=Non
     return st, out, iout
 
 
+def rff_gamma_shape(kind):
+    """Shape nu of the Gamma(nu, 1) draws g that gp_mll_and_grad_rff expects for a kernel
+    (None: the RBF needs none)."""
+    return {RBF: None, MATERN32: 1.5, MATERN52: 2.5, RATQUAD: 1.0}[kind]
+
+
+def gp_mll_and_grad_rff(prob, y, m, n_probes, o, eps, g=None, eps_override=None,
+                        iters_override=None, workspace=None, out=None, iout=None):
+    """The estimator with a random Fourier feature preconditioner of 2m features built
+    from the draws eps (m, d) ~ N(0, 1) and g (m,) ~ Gamma(nu, 1) (Matern-nu), Gamma(1, 1)
+    (rational quadratic) or None (RBF).  Returns (status, out, iout) device tensors,
+    laid out as for gp_mll_and_grad with k = 2m."""
+    lib = load()
+    t = n_probes + 1
+    k = 2 * m
+    yd = torch.as_tensor(y).to(device=prob.device, dtype=prob.dtype).contiguous()
+    ed = torch.as_tensor(eps, dtype=torch.float64).to(prob.device).contiguous()
+    if tuple(ed.shape) != (m, prob.d):
+        raise ValueError(f"eps has shape {tuple(ed.shape)}, not (m, d) = {(m, prob.d)}")
+    gd = None
+    if g is not None:
+        gd = torch.as_tensor(g, dtype=torch.float64).to(prob.device).contiguous()
+        if gd.numel() != m:
+            raise ValueError(f"g has {gd.numel()} entries, not m = {m}")
+    if out is None:
+        out = torch.empty(out_len(prob.p, n_probes), dtype=torch.float64, device=prob.device)
+    if iout is None:
+        iout = torch.empty(2 + t + max(k, 1), dtype=torch.int32, device=prob.device)
+    eo = io = None
+    if eps_override is not None:
+        eo = torch.as_tensor(eps_override)
+        if tuple(eo.shape) != (k + prob.n, n_probes):
+            raise ValueError(f"eps_override has shape {tuple(eo.shape)}, not "
+                             f"(k + n, n_probes) = {(k + prob.n, n_probes)}")
+        eo = eo.to(device=prob.device, dtype=torch.int8).t().contiguous()
+    if iters_override is not None:
+        io = torch.as_tensor(iters_override, dtype=torch.int32).reshape(-1)
+        if io.numel() != t:
+            raise ValueError(f"iters_override has {io.numel()} entries, not t = {t}")
+        io = io.to(prob.device).contiguous()
+    ws = (workspace or _WS).get(gp_workspace_size(FN_MLL_AND_GRAD, prob.n, prob.d, k, t,
+                                                  prob.precision, o.max_iter), prob.device)
+    st = _check("gp_mll_and_grad_rff",
+                lib.gp_mll_and_grad_rff(prob.cref(), _ptr(yd), m, n_probes, _ptr(ed), _ptr(gd),
+                                        _ptr(eo), _ptr(io), _ptr(out), _ptr(iout),
+                                        ctypes.byref(o), _ptr(ws), ws.numel(), _stream()))
+    return st, out, iout
+
+
 def gp_autotune(prob, V, workspace=None):
     """Tune the tensor-core product's launch configuration for this shape; returns
     (W, {chunks, b_ring, v_ring, candidates})."""
@@ -496,7 +547,8 @@ def mvm_timing_read():
 
 def phase_timing_read(phase):
     """(total ms, brackets) of a timed phase since the last read: 0 = kernel-matrix
-    products, 1 = the gradient contraction (one bracket per evaluation)."""
+    products, 1 = the gradient contraction (one bracket per evaluation), 2 = a CG
+    iteration's work outside its products (two brackets per iteration, eager calls)."""
     ms = ctypes.c_double(0.0)
     cnt = ctypes.c_int64(0)
     _check("gp_phase_timing_read",

@@ -172,6 +172,15 @@ def synthetic_study(kind, d, n=10000, seed=0):
                    n_probes=128, tol=1e-10, max_iter=2000, precision=FP64, seed=seed)
 
 
+def rff_draws(m, d, shape, seed=0):
+    """Seeded draws for a random Fourier feature preconditioner: eps (m, d) standard
+    normal and g (m,) from Gamma(shape, 1), or None when shape is None."""
+    rng = np.random.default_rng(10_000 + seed)
+    eps = rng.standard_normal((m, d))
+    g = rng.gamma(shape, 1.0, m) if shape is not None else None
+    return eps, g
+
+
 def subsample(prob, n, seed=1):
     """A smaller problem drawn from the same workload (rows chosen at random)."""
     if n >= prob.n:
