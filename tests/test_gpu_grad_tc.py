@@ -17,7 +17,7 @@ is identical in both (the contraction runs after it), so:
   problem; 4.8e-4 of it from the exponent tile alone), and within 1.2e-4 without the
   exponent's error; the test allows 2e-3;
 * every estimator result, and each gradient entry against 1/2 (|quad_p| + |trace_p|),
-  is within the spec mixed-precision bound of 5e-3 of the oracle.
+  is within the mixed-precision bound of 5e-3 of the oracle.
 """
 import numpy as np
 import pytest

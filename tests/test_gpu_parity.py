@@ -21,7 +21,7 @@ itself moves when its kernel products are perturbed by rounding-sized amounts
     (all of it in y^T u) and 1.9e-6 on gradient entries, hence 3e-7 and 1e-5 there;
   * the same workload with CG run to 1e-10: 2.8e-12 and 1.6e-10, hence 5e-11 and
     3e-9 (the tight FP64 check of the whole estimator).
-In FP32 the benchmark spec's bound of 1e-4 holds on every result when CG runs to a tight
+In FP32 the bound of 1e-4 holds on every result when CG runs to a tight
 tolerance (test_estimator_matern52_ard_fp32_tight); at the Matern-5/2 workload's
 own tolerance of 1e-3 the oracle's gradients move by up to 5.8e-4 under
 FP32-sized perturbations of its products (and 2.5e-5 under FP64-sized ones), so
@@ -327,7 +327,7 @@ def test_estimator_matern52_ard_fp32():
 
 
 def test_estimator_matern52_ard_fp32_tight():
-    """Same workload with CG run to 1e-5: every result within the benchmark spec's 1e-4."""
+    """Same workload with CG run to 1e-5: every result within the FP32 bound of 1e-4."""
     p = workloads.subsample(workloads.c2_matern52_ard(n=20000), 2500)
     p.tol = 1e-5
     p.recompute_every = 20

@@ -9,7 +9,7 @@ Bounds come from the arithmetic:
 * W = K V: P = k(S)/s is rounded to FP16 (relative error <= 2^-11), V is carried as
   FP16 hi + lo of a power-of-two scaled column (~2^-22), FP32 accumulation, so
   |W_i - W_ref_i| <= (2^-11 + small) (|K| |V|)_i; the test allows 2^-10 (|K||V|)_i.
-* estimator results in mixed precision: the benchmark spec's bound of 5e-3 relative per
+* estimator results in mixed precision: the mixed-precision bound of 5e-3 relative per
   result (values; gradient entries against 1/2(|quad_p| + |trace_p|)).
 """
 import numpy as np
