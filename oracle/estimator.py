@@ -31,7 +31,8 @@ Readings of the paper used here (the paper is silent or ambiguous on these):
 * ``rank_floor`` stops the pivoted Cholesky at a residual of rank_floor * max K_ii
   (pivchol.py); a comparison with a factor formed in precision u passes n u.
 * ``rff = (eps, g)`` replaces the partial Cholesky factor by random Fourier features
-  (Tab. 2; features.py), k = 2m columns, with dP_hat at frozen draws.
+  (Tab. 2; features.py), k = 2m columns, with dP_hat at frozen draws; ``qff = mbar``
+  by the quadrature Fourier features of the RBF kernel (mbar^d columns).
 * dP_hat is taken at frozen pivots (woodbury.NystromDerivative).
 """
 import numpy as np
@@ -42,19 +43,26 @@ from . import features, kernels, lanczos, mbcg, pivchol, probes, woodbury
 def mll_and_grad(kind, X, y, theta, ard, k, n_probes, tol, max_iter, seed=0,
                  recompute_every=0, pivchol_tol=0.0, piv_override=None,
                  iters_override=None, eps=None, literal=False, with_grad=True, rank_floor=0.0,
-                 rff=None):
+                 rff=None, qff=None):
     X = np.asarray(X, np.float64)
     y = np.asarray(y, np.float64)
     n = X.shape[0]
     op = kernels.KernelOperator(kind, X, theta, ard)
     s2 = op.s2
 
-    if rff is None:
+    if rff is None and qff is None:
         L, piv, rank, _ = pivchol.pivoted_cholesky(op, k, pivchol_tol, piv_override, rank_floor)
         dprec = None
     else:
-        # random Fourier features (features.py): k = 2m columns from the draws (eps, g)
-        dprec = features.RandomFourier(kind, X, theta, ard, *rff)
+        # random Fourier features from the draws (eps, g), or the quadrature features of
+        # qff = mbar nodes per dimension (features.py): k = 2m columns
+        if rff is not None:
+            dprec = features.RandomFourier(kind, X, theta, ard, *rff)
+        else:
+            if kind != kernels.RBF:
+                raise ValueError("quadrature Fourier features are defined for the RBF kernel")
+            U, w = features.hermite_grid(qff, X.shape[1])
+            dprec = features.RandomFourier(kind, X, theta, ard, U=U, weights=w)
         L, piv, rank = dprec.Phi, np.zeros(0, np.int64), dprec.Phi.shape[1]
         k = rank
     logdetP = woodbury.logdet(L, s2)

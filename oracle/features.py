@@ -54,26 +54,53 @@ def frequencies(kind, eps, g):
     return rho[:, None] * eps
 
 
+def hermite_grid(mbar, d):
+    """Quadrature Fourier features (Tab. 2 "QFF", Prop. "QFF approximation quality",
+    after Mutny and Krause 2018) for the RBF kernel: E_w[cos(w . D)] with w ~ N(0, I_d)
+    by the tensor-product Gauss-Hermite rule of mbar nodes per dimension (numpy's
+    hermgauss, weight exp(-t^2)): w = sqrt(2) t, weight prod_i w_i / sqrt(pi).  The rule
+    is symmetric, and w and -w give the same cos(w . D), so each pair is kept once with
+    twice the weight (mbar even: no zero node).  Returns (U, weights): mbar^d / 2
+    frequencies in units of 1 / l and their weights, which sum to 1."""
+    if mbar % 2:
+        raise ValueError("mbar must be even")
+    t, w = np.polynomial.hermite.hermgauss(mbar)
+    grids = np.meshgrid(*([np.sqrt(2.0) * t] * d), indexing="ij")
+    U = np.stack([g.reshape(-1) for g in grids], axis=1)
+    W = np.ones(U.shape[0])
+    for wi in np.meshgrid(*([w / np.sqrt(np.pi)] * d), indexing="ij"):
+        W = W * wi.reshape(-1)
+    # keep the half with a positive first nonzero coordinate (none is zero: mbar even)
+    keep = U[:, 0] > 0
+    return U[keep], 2.0 * W[keep]
+
+
 class RandomFourier:
     """Phi (n x 2m) and its derivatives for the hyperparameters theta (the order of
-    ``kernels.kernel_grad_blocks`` followed by the noise)."""
+    ``kernels.kernel_grad_blocks`` followed by the noise).  With ``eps, g`` the random
+    features above (weights 1/m); with ``U, weights`` given instead, any weighted
+    frequency set (the quadrature features of ``hermite_grid``)."""
 
-    def __init__(self, kind, X, theta, ard, eps, g):
+    def __init__(self, kind, X, theta, ard, eps=None, g=None, U=None, weights=None):
         self.X = np.asarray(X, np.float64)
         self.n, self.d = self.X.shape
         self.ard = ard
         self.ls, self.s, self.s2 = kernels.unpack(theta, self.d, ard)
         self.p = kernels.n_hyper(self.d, ard)
-        self.U = frequencies(kind, eps, g)                      # m x d
+        if U is None:
+            self.U = frequencies(kind, eps, g)                  # m x d
+            weights = np.full(self.U.shape[0], 1.0 / self.U.shape[0])
+        else:
+            self.U = np.asarray(U, np.float64)
         self.m = self.U.shape[0]
         # x~ = (x - mean x) / l: the origin of the features is the input mean (any fixed
         # shift rotates each cos / sin pair and leaves Phi Phi^T unchanged)
         self.Xs = (self.X - self.X.mean(axis=0)) / self.ls
         arg = self.Xs @ self.U.T                                # n x m
-        self.amp = np.sqrt(self.s / self.m)
+        self.amp = np.sqrt(self.s * np.asarray(weights, np.float64))[None, :]
         self.cos, self.sin = np.cos(arg), np.sin(arg)
         self.arg = arg
-        self.Phi = self.amp * np.hstack([self.cos, self.sin])
+        self.Phi = np.hstack([self.amp * self.cos, self.amp * self.sin])
 
     def dphi(self, q):
         """dPhi / dtheta_q (n x 2m) for q < p - 1."""
@@ -85,7 +112,7 @@ class RandomFourier:
             darg = -(self.Xs[:, q][:, None] * self.U[:, q][None, :]) / self.ls[q]
         else:
             darg = -self.arg / self.ls[0]
-        return self.amp * np.hstack([-self.sin * darg, self.cos * darg])
+        return np.hstack([-self.amp * self.sin * darg, self.amp * self.cos * darg])
 
     def apply(self, q, V):
         """dP_hat / dtheta_q @ V."""

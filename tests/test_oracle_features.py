@@ -10,6 +10,10 @@
   and E[trace estimate] = tr(K_hat^-1 dK_hat_p).
 * The rate of Prop. "RFF approximation quality": the Frobenius error of P_hat falls
   like k^-1/2 (16x the features, about 4x smaller).
+* Quadrature Fourier features (RBF): the folded Gauss-Hermite tensor rule has the
+  moments of N(0, I_d); Phi Phi^T converges to K exponentially in the nodes per
+  dimension (Prop. "QFF approximation quality"); finite differences; unbiasedness by
+  enumeration as above.
 """
 import itertools
 
@@ -125,3 +129,78 @@ def test_error_falls_like_inverse_square_root_of_k():
 
     ratio = mean_err(16) / mean_err(256)    # k = 32 vs 512 features
     assert 3.0 <= ratio <= 5.3, ratio
+
+
+# ---- quadrature Fourier features (Tab. 2 "QFF", RBF kernel) ---------------------------
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_hermite_grid_moments(d):
+    """The folded tensor rule integrates against N(0, I_d): weights sum to 1, E[w_i^2] = 1,
+    E[w_i^4] = 3, E[w_i^2 w_j^2] = 1 (i != j), and it is exact for cos(w . D) up to the
+    rule's degree (checked through the moments that cos's Taylor terms need)."""
+    U, W = features.hermite_grid(6, d)
+    assert U.shape == (6 ** d // 2, d) and np.all(W > 0)
+    assert abs(W.sum() - 1.0) < 1e-14
+    for i in range(d):
+        assert abs(np.sum(W * U[:, i] ** 2) - 1.0) < 1e-13
+        assert abs(np.sum(W * U[:, i] ** 4) - 3.0) < 1e-12
+        for j in range(i + 1, d):
+            assert abs(np.sum(W * U[:, i] ** 2 * U[:, j] ** 2) - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("d,mbars,last", [(1, (4, 8, 16, 32), 1e-12), (2, (4, 8, 16), 1e-8)])
+def test_quadrature_features_converge_to_the_kernel(d, mbars, last):
+    """Prop. "QFF approximation quality": the error of Phi Phi^T falls exponentially in
+    the nodes per dimension."""
+    X = _points(25, d, 9)
+    theta = np.concatenate([np.full(d, 0.35), [1.1, 0.01]])
+    K = kernels.kernel_block(kernels.RBF, X, X, theta, True)
+    errs = []
+    for mb in mbars:
+        f = features.RandomFourier(kernels.RBF, X, theta, True,
+                                   *(None, None), *features.hermite_grid(mb, d))
+        errs.append(np.max(np.abs(f.Phi @ f.Phi.T - K)))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < last, errs
+
+
+@pytest.mark.parametrize("ard", [True, False])
+def test_quadrature_feature_derivative(ard):
+    X = _points(12, 2, 10)
+    theta = np.array([0.4, 0.6, 1.2, 0.02]) if ard else np.array([0.5, 1.2, 0.02])
+    U, W = features.hermite_grid(6, 2)
+    f = features.RandomFourier(kernels.RBF, X, theta, ard, U=U, weights=W)
+    for q in range(f.p - 1):
+        h = 1e-6 * theta[q]
+        tp, tm = theta.copy(), theta.copy()
+        tp[q] += h
+        tm[q] -= h
+        fd = (features.RandomFourier(kernels.RBF, X, tp, ard, U=U, weights=W).Phi
+              - features.RandomFourier(kernels.RBF, X, tm, ard, U=U, weights=W).Phi) / (2 * h)
+        np.testing.assert_allclose(f.dphi(q), fd, rtol=1e-6, atol=1e-8)
+
+
+def test_estimator_unbiased_with_quadrature_features():
+    n = 4                                   # mbar = 4 in 1-D: k = 4 features
+    X = _points(n, 1, 11)
+    y = np.array([0.5, -0.2, 1.1, -0.7])
+    theta = np.array([0.5, 1.1, 0.2])
+    U, W = features.hermite_grid(4, 1)
+    f = features.RandomFourier(kernels.RBF, X, theta, True, U=U, weights=W)
+    Kh = kernels.khat_dense(kernels.RBF, X, theta, True)
+    P = theta[-1] * np.eye(n) + f.Phi @ f.Phi.T
+    dK = kernels.dkhat_dense(kernels.RBF, X, theta, True)
+    acc_s, acc_t, cnt = 0.0, 0.0, 0
+    for bits in itertools.product([-1.0, 1.0], repeat=4 + n):
+        e1 = np.array(bits[:4])[:, None]
+        e2 = np.array(bits[4:])[:, None]
+        out = estimator.mll_and_grad(kernels.RBF, X, y, theta, True, 0, 1, 1e-15, 60,
+                                     eps=(e1, e2), qff=4)
+        acc_s = acc_s + out["stoch"]
+        acc_t = acc_t + out["trace_p"] - out["trP_p"]
+        cnt += 1
+    want_s = np.linalg.slogdet(Kh)[1] - np.linalg.slogdet(P)[1]
+    Khi, Pi = np.linalg.inv(Kh), np.linalg.inv(P)
+    want_t = np.array([np.trace(Khi @ dK[q]) - np.trace(Pi @ f.dense(q)) for q in range(f.p)])
+    assert abs(acc_s / cnt - want_s) <= 1e-10 * max(1.0, abs(want_s))
+    np.testing.assert_allclose(acc_t / cnt, want_t, rtol=1e-9, atol=1e-10)
