@@ -567,7 +567,7 @@ def run_synthetic(args):
 def run_decay(args):
     """The residual-decay experiment (Fig. 2; rates of Tab. 2): as the rank k of the partial
     Cholesky preconditioner (or the number of random Fourier features, mean over four
-    draws) grows, log det P_hat_k -> log det K_hat and tr(P_hat_k^-1 dP_hat_k) ->
+    draws, or of quadrature Fourier features for the RBF kernel) grows, log det P_hat_k -> log det K_hat and tr(P_hat_k^-1 dP_hat_k) ->
     tr(K_hat^-1 dK_hat) for every hyperparameter, at the rate at which P_hat_k -> K_hat
     (the residual trace tr(K - L L^T) / tr K).  Four n = 1,000 problems of the synthetic
     study's generator (RBF and Matern-3/2, d = 1 and 3), FP64; the exact values are
@@ -620,6 +620,22 @@ def run_decay(args):
                    "rank": k, "residual_trace": float("nan"), "logdet_rel_err": acc[0],
                    "trace_rel_err": {"lengthscale": acc[1], "outputscale": acc[2],
                                      "noise": acc[3]}, "draws": 4}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        # quadrature Fourier features (RBF only; Tab. 2: error ~ exp(-b k^(1/d)))
+        if kind != workloads.RBF:
+            continue
+        for mbar in ((4, 8, 16, 32) if d == 1 else (2, 4, 6, 8)):
+            k = mbar ** d
+            st, out, iout = gp.gp_mll_and_grad_qff(prob, p.y, mbar, 1, o)
+            r = gp.unpack(out, iout, prob.p, 1, k)
+            e_tr = [abs(float(a) - float(b)) / abs(float(b))
+                    for a, b in zip(r["trP_p"], ex["trace_p"])]
+            row = {"kernel": names[kind], "d": d, "n": p.n, "preconditioner": "qff", "k": k,
+                   "rank": r["rank"], "residual_trace": float("nan"),
+                   "logdet_rel_err": abs(r["logdetP"] - ex["logdet"]) / abs(ex["logdet"]),
+                   "trace_rel_err": {"lengthscale": e_tr[0], "outputscale": e_tr[1],
+                                     "noise": e_tr[2]}, "nodes_per_dim": mbar}
             rows.append(row)
             print(json.dumps(row), flush=True)
     print("| kernel | d | preconditioner | k (rank) | tr(K - LL^T) / tr K | log det rel. err | "

@@ -240,7 +240,8 @@ gp_status gp_mll_and_grad(const gp_problem* prob, const void* y, int32_t k,
  *   Phi[a, j] = sqrt(s/m) cos(u_j . x~_a),  Phi[a, m + j] = sqrt(s/m) sin(u_j . x~_a),
  * x~ = (x - mean x) / l (elementwise for ARD; the inputs' mean as the origin, which
  * leaves P_hat unchanged and fixes the probes), u_j = rho_j eps_j drawn from the
- * kernel's spectral density: RBF rho = 1; Matern-3/2 and -5/2 rho = sqrt(nu / g_j) with g_j ~ Gamma(nu, 1);
+ * kernel's spectral density: RBF rho = 1; Matern-3/2 and -5/2 rho = sqrt(nu / g_j)
+ * with g_j ~ Gamma(nu, 1);
  * rational quadratic (alpha = 1) rho = sqrt(g_j) with g_j ~ Gamma(1, 1).
  * eps: device, m x d doubles (row-major), standard-normal draws; g: device, m doubles
  * (may be NULL for the RBF).  The gradient's preconditioner terms take dP_hat at these
@@ -253,6 +254,28 @@ gp_status gp_mll_and_grad_rff(const gp_problem* prob, const void* y, int32_t m,
                               const int8_t* eps_override, const int32_t* iters_override,
                               double* out, int32_t* iout, const gp_opts* opts, void* ws,
                               size_t ws_bytes, gp_stream_t stream);
+
+/* The same estimator with the quadrature Fourier feature preconditioner of Tab. 2
+ * ("QFF"; Prop. "QFF approximation quality", after Mutny and Krause 2018), RBF kernel
+ * only: E_w[cos(w . D)], w ~ N(0, I_d), by the tensor-product Gauss-Hermite rule of
+ * mbar nodes per dimension (mbar even), each pair w, -w kept once with twice the weight:
+ * m = mbar^d / 2 frequencies u_j (multi-indices in row-major order over ascending
+ * nodes, the one with a positive first coordinate kept) with weights w_j, and k =
+ * mbar^d features sqrt(s w_j) cos(u_j . x~), sqrt(s w_j) sin(u_j . x~), x~ = (x - mean
+ * x) / l.  The rule is computed on the host and copied in; the call synchronises with
+ * `stream` and cannot be captured into a graph.  Outputs, statuses and workspace as
+ * for gp_mll_and_grad with k = mbar^d (<= min(n, the largest k)).                    */
+gp_status gp_mll_and_grad_qff(const gp_problem* prob, const void* y, int32_t mbar,
+                              int32_t n_probes, const int8_t* eps_override,
+                              const int32_t* iters_override, double* out, int32_t* iout,
+                              const gp_opts* opts, void* ws, size_t ws_bytes,
+                              gp_stream_t stream);
+
+/* The quadrature rule of gp_mll_and_grad_qff, on the host: writes the m = mbar^d / 2
+ * frequencies (U, m x d doubles, row-major; NULL to skip) and their weights (W, m
+ * doubles; NULL to skip) and returns m, or a negative gp_status (mbar odd or < 2, d out
+ * of range, mbar^d > 4096).                                                          */
+int32_t gp_qff_rule(int32_t mbar, int32_t d, double* U, double* W);
 
 /* Batched estimator: n_problems independent problems (each its own n, d, X,
  * hyperparameters and precision; shared k, n_probes and opts; problem i draws its

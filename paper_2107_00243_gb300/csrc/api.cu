@@ -408,7 +408,8 @@ struct MllPlan {
   T* L;
   int* pivots;
   int* rank;
-  double* featU;     // random Fourier features: m x d frequencies (m <= k / 2)
+  double* featU;     // Fourier features: m x d frequencies (m <= k / 2)
+  double* featW;     // and their m weights
   T* B;
   T* PinvB;
   double* wts;
@@ -425,6 +426,7 @@ void plan_mll(Arena& A, const Prob& pb, int k, int nl, int max_iter, MllPlan<T>&
   plan_cg<T>(A, pb, k, t, max_iter, P.cg);
   plan_prec(A, pb, k, nl, P.prec);
   P.featU = A.take<double>((size_t)std::max(k / 2, 1) * pb.d);
+  P.featW = A.take<double>((size_t)std::max(k / 2, 1));
   P.use_tg = P.mvm.use_tc && tc_grad_supported(pb, t);
   P.tg = TcGradBufs{};
   if (P.use_tg) {
@@ -477,8 +479,8 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   GP_TRY(run_prep<T>(pb, P.mvm.prep, st));
   const void* Xs = P.mvm.prep.pr.Xs;
   if (feat) {
-    // S2': random Fourier features (Tab. 2) as the low-rank factor: rank k = 2m, no pivots
-    GP_TRY(rff_build<T>(pb, Xs, feat->m, feat->eps, feat->g, P.featU, P.L, pb.n, st));
+    // S2': Fourier features (Tab. 2) as the low-rank factor: rank k = 2m, no pivots
+    GP_TRY(rff_build<T>(pb, Xs, *feat, P.featU, P.featW, P.L, pb.n, st));
     GP_CUDA_TRY(cudaMemsetAsync(P.pivots, 0xff, sizeof(int) * (size_t)k, st));
     set_int_kernel<<<1, 1, 0, st>>>(P.rank, k);
     GP_LAUNCH_CHECK();
@@ -554,8 +556,8 @@ gp_status mll_impl(const Prob& pb, const T* y, int k, int nl, const int8_t* eps,
   if (timed) mvm_timing_end(st, 1);
   // S10: preconditioner terms with W = P^-1 z_i (columns 1..l of PinvB)
   if (feat) {
-    GP_TRY(feature_terms<T>(pb, Xs, P.L, pb.n, feat->m, P.featU, P.PinvB + pb.n, pb.n, nl,
-                            P.core.Cinv, P.prec, out + GP_OUT_TRP(pb.p),
+    GP_TRY(feature_terms<T>(pb, Xs, P.L, pb.n, feat->m, P.featU, P.featW, P.PinvB + pb.n,
+                            pb.n, nl, P.core.Cinv, P.prec, out + GP_OUT_TRP(pb.p),
                             out + GP_OUT_PROBEP(pb.p), st));
   } else {
     GP_TRY(precond_terms<T>(pb, Xs, P.L, pb.n, k, P.pivots, P.rank, P.PinvB + pb.n, pb.n, nl,
@@ -1011,12 +1013,68 @@ extern "C" gp_status gp_mll_and_grad_rff(const gp_problem* prob, const void* y, 
   GP_TRY(check_ws(ws, ws_bytes,
                   gp_workspace_size(GP_FN_MLL_AND_GRAD, pb.n, pb.d, k, t, pb.prec, opts->max_iter)));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const FeatSpec feat{m, eps, g};
+  const FeatSpec feat{m, eps, g, nullptr, nullptr};
   if (pb.prec == GP_FP64)
     return mll_impl<double>(pb, (const double*)y, k, n_probes, eps_override, nullptr,
                             iters_override, out, iout, *opts, ws, ws_bytes, st, 0, &feat);
   return mll_impl<float>(pb, (const float*)y, k, n_probes, eps_override, nullptr,
                          iters_override, out, iout, *opts, ws, ws_bytes, st, 0, &feat);
+}
+
+extern "C" int32_t gp_qff_rule(int32_t mbar, int32_t d, double* U, double* W) {
+  GP_REQUIRE(mbar >= 2 && mbar % 2 == 0, "mbar=%d must be even and >= 2", mbar);
+  GP_REQUIRE(d >= 1 && d <= kMaxD, "d=%d out of range [1, %d]", d, kMaxD);
+  int64_t total = 1;
+  for (int i = 0; i < d && total <= 2 * (int64_t)kMaxK; ++i) total *= mbar;
+  GP_REQUIRE(total <= 2 * (int64_t)kMaxK, "mbar^d exceeds %d", 2 * kMaxK);
+  std::vector<double> u, w;
+  qff_table(mbar, d, u, w);
+  if (U) std::copy(u.begin(), u.end(), U);
+  if (W) std::copy(w.begin(), w.end(), W);
+  return (int32_t)w.size();
+}
+
+extern "C" gp_status gp_mll_and_grad_qff(const gp_problem* prob, const void* y, int32_t mbar,
+                                         int32_t n_probes, const int8_t* eps_override,
+                                         const int32_t* iters_override, double* out,
+                                         int32_t* iout, const gp_opts* opts, void* ws,
+                                         size_t ws_bytes, gp_stream_t stream) {
+  GP_TRY(check_problem(prob));
+  GP_TRY(check_opts(opts));
+  GP_REQUIRE(y && out && iout, "y, out or iout is NULL");
+  GP_REQUIRE(prob->kind == GP_RBF, "quadrature Fourier features need the RBF kernel");
+  GP_REQUIRE(mbar >= 2 && mbar % 2 == 0, "mbar=%d must be even and >= 2", mbar);
+  int64_t k = 1;
+  for (int i = 0; i < prob->d && k <= kMaxK; ++i) k *= mbar;
+  GP_REQUIRE(k <= kMaxK && k <= prob->n, "mbar^d = %lld features exceed min(n, %d)",
+             (long long)k, kMaxK);
+  GP_REQUIRE(n_probes >= 0 && n_probes + 1 <= kMaxT, "n_probes=%d out of range", n_probes);
+  Prob pb = make_prob(prob);
+  const int t = n_probes + 1;
+  GP_REQUIRE(!((pb.prec == GP_BF16 || pb.prec == GP_TF32) && !tc_supported(pb, t)),
+             "tensor-core precision does not support this shape");
+  GP_TRY(check_ws(ws, ws_bytes, gp_workspace_size(GP_FN_MLL_AND_GRAD, pb.n, pb.d, (int)k, t,
+                                                  pb.prec, opts->max_iter)));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GP_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  GP_REQUIRE(cap == cudaStreamCaptureStatusNone,
+             "gp_mll_and_grad_qff copies its quadrature table from the host: not capturable");
+  std::vector<double> U, W;
+  qff_table(mbar, pb.d, U, W);
+  const int m = (int)W.size();
+  GP_REQUIRE(2 * m == (int)k, "internal: %d frequencies for %lld features", m, (long long)k);
+  const FeatSpec feat{m, nullptr, nullptr, U.data(), W.data()};
+  gp_status r;
+  if (pb.prec == GP_FP64)
+    r = mll_impl<double>(pb, (const double*)y, (int)k, n_probes, eps_override, nullptr,
+                         iters_override, out, iout, *opts, ws, ws_bytes, st, 0, &feat);
+  else
+    r = mll_impl<float>(pb, (const float*)y, (int)k, n_probes, eps_override, nullptr,
+                        iters_override, out, iout, *opts, ws, ws_bytes, st, 0, &feat);
+  // the host table must outlive its copies
+  GP_CUDA_TRY(cudaStreamSynchronize(st));
+  return r;
 }
 
 // ---- batched evaluation --------------------------------------------------------------

@@ -3,6 +3,8 @@
 
 #include "common.cuh"
 
+#include <vector>
+
 namespace gp {
 
 constexpr int kPrepBlocks = 256;
@@ -202,20 +204,28 @@ struct PrecBufs {
 // Random Fourier feature preconditioner: m frequencies u_j = rho_j eps_j (U, m x d FP64)
 // from the standard-normal draws eps (m x d, row-major) and the Gamma draws g (m; unused
 // for the RBF), and the n x 2m feature matrix Phi (ld ldp) in the problem precision.
+// Or a deterministic weighted set (hostU: m x d frequencies, hostW: m weights, host
+// memory; the quadrature features of qff_table), copied to the device.
 struct FeatSpec {
   int m;
   const double* eps;
   const double* g;
+  const double* hostU;
+  const double* hostW;
 };
 template <class T>
-gp_status rff_build(const Prob& pb, const void* Xs, int m, const double* eps, const double* g,
-                    double* U, T* Phi, int64_t ldp, cudaStream_t st);
-// trP and probeP of P_hat = sigma^2 I + Phi Phi^T (dP_hat at frozen draws).
+gp_status rff_build(const Prob& pb, const void* Xs, const FeatSpec& f, double* U, double* wt,
+                    T* Phi, int64_t ldp, cudaStream_t st);
+// trP and probeP of P_hat = sigma^2 I + Phi Phi^T (dP_hat at frozen frequencies).
 template <class T>
 gp_status feature_terms(const Prob& pb, const void* Xs, const T* Phi, int64_t ldp, int m,
-                        const double* U, const T* W, int64_t ldw, int n_probes,
-                        const double* Cinv, const PrecBufs& b, double* trP, double* probeP,
-                        cudaStream_t st);
+                        const double* U, const double* wt, const T* W, int64_t ldw,
+                        int n_probes, const double* Cinv, const PrecBufs& b, double* trP,
+                        double* probeP, cudaStream_t st);
+// Gauss-Hermite rule (weight exp(-t^2)) of mbar nodes, and the folded d-dimensional grid
+// of the quadrature Fourier features (m = mbar^d / 2 frequencies, weights summing to 1).
+void hermite_rule(int mbar, std::vector<double>& t, std::vector<double>& w);
+void qff_table(int mbar, int d, std::vector<double>& U, std::vector<double>& W);
 template <class T>
 gp_status precond_terms(const Prob& pb, const void* Xs, const T* L, int64_t ldl, int k,
                         const int* piv, const int* rank, const T* W, int64_t ldw, int n_probes,

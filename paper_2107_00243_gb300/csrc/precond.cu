@@ -20,6 +20,10 @@
 // replace p - 1 passes of an n x k x (k + l) product.  Everything k x k is FP64.
 #include "ops.h"
 
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 namespace gp {
 namespace {
 
@@ -318,8 +322,9 @@ __global__ void sumsq_kernel(int64_t n, int nl, const T* __restrict__ W, int64_t
 }
 
 // ---- random Fourier feature preconditioner (Tab. 2 "RFF") -----------------------------
-// P_hat = sigma^2 I + Phi Phi^T with m frequencies u_j (in units of 1 / l) and k = 2m
-// features  Phi[a, j] = sqrt(s/m) cos(u_j . x~_a),  Phi[a, m + j] = sqrt(s/m) sin(u_j . x~_a)
+// P_hat = sigma^2 I + Phi Phi^T with m frequencies u_j (in units of 1 / l), weights w_j
+// (1/m for random features) and k = 2m features
+//   Phi[a, j] = sqrt(s w_j) cos(u_j . x~_a),  Phi[a, m + j] = sqrt(s w_j) sin(u_j . x~_a)
 // (x~ = (x - mean x) / l, the centred inputs of S1: a shift of the origin only turns each
 // cos / sin pair, so Phi Phi^T is the same).  By Bochner's theorem E[Phi Phi^T] = K when
 // u_j is drawn from the kernel's spectral density, written as a Gaussian scale mixture
@@ -332,10 +337,12 @@ __global__ void sumsq_kernel(int64_t n, int nl, const T* __restrict__ W, int64_t
 constexpr int kFeatChunk = 32;    // frequencies staged in shared memory per step
 
 __global__ void rff_freq_kernel(int kind, int m, int d, const double* __restrict__ eps,
-                                const double* __restrict__ g, double* __restrict__ U) {
+                                const double* __restrict__ g, double* __restrict__ U,
+                                double* __restrict__ wt) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * d) return;
   const int j = e / d;
+  if (e % d == 0) wt[j] = 1.0 / m;    // equal weights: E[Phi Phi^T] = K
   double rho = 1.0;
   if (kind == GP_RATQUAD) rho = sqrt(g[j]);
   else if (kind == GP_MATERN32) rho = sqrt(1.5 / g[j]);
@@ -348,6 +355,7 @@ template <class T, int DM>
 __global__ void __launch_bounds__(256) rff_build_kernel(int64_t n, int d, int m,
                                                         const T* __restrict__ Xs,
                                                         const double* __restrict__ U,
+                                                        const double* __restrict__ wt,
                                                         const double* __restrict__ theta, int D,
                                                         T* __restrict__ Phi, int64_t ldp) {
   __shared__ double su[kFeatChunk][DM];
@@ -363,8 +371,8 @@ __global__ void __launch_bounds__(256) rff_build_kernel(int64_t n, int d, int m,
   double xa[DM];
 #pragma unroll
   for (int u = 0; u < DM; ++u) xa[u] = u < d ? (double)Xs[a * d + u] : 0.0;
-  const double amp = sqrt(theta[D] / m);
   for (int jj = 0; jj < jn; ++jj) {
+    const double amp = sqrt(theta[D] * wt[j0 + jj]);
     double arg = 0.0;
 #pragma unroll
     for (int u = 0; u < DM; ++u) arg = fma(su[jj][u], xa[u], arg);
@@ -385,6 +393,7 @@ __global__ void __launch_bounds__(256) rff_contract(int64_t n, int d, int ard, i
                                                     const double* __restrict__ theta,
                                                     const T* __restrict__ Xs,
                                                     const double* __restrict__ U,
+                                                    const double* __restrict__ wt,
                                                     const T* __restrict__ Z1,
                                                     const T* __restrict__ Z2,
                                                     double* __restrict__ part) {
@@ -395,7 +404,6 @@ __global__ void __launch_bounds__(256) rff_contract(int64_t n, int d, int ard, i
   double xa[DM];
 #pragma unroll
   for (int u = 0; u < DM; ++u) xa[u] = (a < n && u < d) ? (double)Xs[a * d + u] : 0.0;
-  const double amp = sqrt(theta[D] / m);
   double e1[NQ], e2[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) { e1[q] = 0.0; e2[q] = 0.0; }
@@ -410,6 +418,7 @@ __global__ void __launch_bounds__(256) rff_contract(int64_t n, int d, int ard, i
     if (a >= n) continue;
     for (int jj = 0; jj < jn; ++jj) {
       const int j = j0 + jj;
+      const double amp = sqrt(theta[D] * wt[j]);
       double arg = 0.0;
 #pragma unroll
       for (int u = 0; u < DM; ++u) arg = fma(su[jj][u], xa[u], arg);
@@ -528,22 +537,103 @@ gp_status precond_terms(const Prob& pb, const void* Xs_, const T* L, int64_t ldl
   return GP_OK;
 }
 
+// ---- quadrature Fourier features (Tab. 2 "QFF", RBF kernel) -----------------------------
+// E_w[cos(w . D)] with w ~ N(0, I_d) by the tensor-product Gauss-Hermite rule (weight
+// exp(-t^2), w = sqrt(2) t, weights prod w_i / sqrt(pi)).  The mbar nodes are the
+// eigenvalues of the Jacobi matrix of the Hermite recurrence (zero diagonal, off-diagonal
+// sqrt(k / 2)), found by bisection on Sturm counts (the number of negative pivots of the
+// LDL^T factorisation of J - x I is the number of eigenvalues below x).  The weights are
+// Christoffel numbers 1 / sum_k psi_k(t)^2 of the orthonormal Hermite functions,
+// psi_0 = pi^-1/4, psi_{k+1} = sqrt(2 / (k+1)) t psi_k - sqrt(k / (k+1)) psi_{k-1}.
+namespace {
+int sturm_below(int mbar, double x) {
+  int cnt = 0;
+  double q = -x;                                       // diagonal 0
+  for (int i = 0; i < mbar; ++i) {
+    if (i > 0) q = -x - (0.5 * i) / q;                 // off-diagonal^2 = i / 2
+    if (q == 0.0) q = -1e-300;                         // on an eigenvalue: count it below
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+}  // namespace
+
+void hermite_rule(int mbar, std::vector<double>& t, std::vector<double>& w) {
+  t.assign(mbar, 0.0);
+  w.assign(mbar, 0.0);
+  const double B = std::sqrt(2.0 * std::max(mbar - 1, 1)) + 1.0;   // Gershgorin bound
+  for (int j = 0; j < mbar; ++j) {
+    double lo = -B, hi = B;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(lo + hi)); ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (sturm_below(mbar, mid) > j) hi = mid;
+      else lo = mid;
+    }
+    t[j] = 0.5 * (lo + hi);
+    double p0 = std::pow(M_PI, -0.25), p1 = 0.0, s2 = p0 * p0;
+    for (int k = 0; k + 1 < mbar; ++k) {
+      const double p2 = std::sqrt(2.0 / (k + 1)) * t[j] * p0 - std::sqrt((double)k / (k + 1)) * p1;
+      p1 = p0;
+      p0 = p2;
+      s2 += p0 * p0;
+    }
+    w[j] = 1.0 / s2;
+  }
+}
+
+// The folded grid: m = mbar^d / 2 frequencies (units of 1 / l, row-major m x d) and
+// weights summing to 1.  Multi-indices in row-major order (last index fastest) over the
+// ascending nodes; of w and -w the one with a positive first coordinate is kept, with
+// twice the weight (mbar even: no zero node).
+void qff_table(int mbar, int d, std::vector<double>& U, std::vector<double>& W) {
+  std::vector<double> t, w;
+  hermite_rule(mbar, t, w);
+  int64_t total = 1;
+  for (int i = 0; i < d; ++i) total *= mbar;
+  U.clear();
+  W.clear();
+  std::vector<int> q(d, 0);
+  for (int64_t e = 0; e < total; ++e) {
+    int64_t r = e;
+    for (int i = d - 1; i >= 0; --i) {
+      q[i] = (int)(r % mbar);
+      r /= mbar;
+    }
+    if (!(t[q[0]] > 0.0)) continue;
+    double wt = 2.0;
+    for (int i = 0; i < d; ++i) {
+      U.push_back(std::sqrt(2.0) * t[q[i]]);
+      wt *= w[q[i]] / std::sqrt(M_PI);
+    }
+    W.push_back(wt);
+  }
+}
+
 template <class T>
-gp_status rff_build(const Prob& pb, const void* Xs_, int m, const double* eps, const double* g,
-                    double* U, T* Phi, int64_t ldp, cudaStream_t st) {
+gp_status rff_build(const Prob& pb, const void* Xs_, const FeatSpec& f, double* U, double* wt,
+                    T* Phi, int64_t ldp, cudaStream_t st) {
   const T* Xs = static_cast<const T*>(Xs_);
-  rff_freq_kernel<<<(unsigned)cdiv((int64_t)m * pb.d, 256), 256, 0, st>>>(pb.kind, m, pb.d, eps,
-                                                                           g, U);
-  GP_LAUNCH_CHECK();
+  const int m = f.m;
+  if (f.hostU) {
+    // a deterministic rule (quadrature features): frequencies and weights from the host
+    GP_CUDA_TRY(cudaMemcpyAsync(U, f.hostU, sizeof(double) * (size_t)m * pb.d,
+                                cudaMemcpyHostToDevice, st));
+    GP_CUDA_TRY(cudaMemcpyAsync(wt, f.hostW, sizeof(double) * (size_t)m, cudaMemcpyHostToDevice,
+                                st));
+  } else {
+    rff_freq_kernel<<<(unsigned)cdiv((int64_t)m * pb.d, 256), 256, 0, st>>>(pb.kind, m, pb.d,
+                                                                             f.eps, f.g, U, wt);
+    GP_LAUNCH_CHECK();
+  }
   const dim3 grid((unsigned)cdiv(pb.n, 256), (unsigned)cdiv(m, kFeatChunk));
   switch (dm_of(pb.d)) {
-    case 4: rff_build_kernel<T, 4><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, pb.theta, pb.D,
+    case 4: rff_build_kernel<T, 4><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, wt, pb.theta, pb.D,
                                                          Phi, ldp); break;
-    case 8: rff_build_kernel<T, 8><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, pb.theta, pb.D,
+    case 8: rff_build_kernel<T, 8><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, wt, pb.theta, pb.D,
                                                          Phi, ldp); break;
-    case 16: rff_build_kernel<T, 16><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, pb.theta, pb.D,
+    case 16: rff_build_kernel<T, 16><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, wt, pb.theta, pb.D,
                                                            Phi, ldp); break;
-    default: rff_build_kernel<T, 32><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, pb.theta, pb.D,
+    default: rff_build_kernel<T, 32><<<grid, 256, 0, st>>>(pb.n, pb.d, m, Xs, U, wt, pb.theta, pb.D,
                                                            Phi, ldp); break;
   }
   GP_LAUNCH_CHECK();
@@ -556,8 +646,9 @@ gp_status rff_build(const Prob& pb, const void* Xs_, int m, const double* eps, c
 // are the same as there.
 template <class T>
 gp_status feature_terms(const Prob& pb, const void* Xs_, const T* Phi, int64_t ldp, int m,
-                        const double* U, const T* W, int64_t ldw, int nl, const double* Cinv,
-                        const PrecBufs& b, double* trP, double* probeP, cudaStream_t st) {
+                        const double* U, const double* wt, const T* W, int64_t ldw, int nl,
+                        const double* Cinv, const PrecBufs& b, double* trP, double* probeP,
+                        cudaStream_t st) {
   const T* Xs = static_cast<const T*>(Xs_);
   const int P = pb.p, k = 2 * m;
   double* wn = b.LtW + (int64_t)k * nl;
@@ -593,13 +684,13 @@ gp_status feature_terms(const Prob& pb, const void* Xs_, const T* Phi, int64_t l
   const int nblk = (int)cdiv(pb.n, 256);
   switch (DM) {
     case 4: rff_contract<T, 4><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.ard, pb.D, m, pb.theta, Xs, U,
-                                                     Z1, Z2, b.dkpart); break;
+                                                     wt, Z1, Z2, b.dkpart); break;
     case 8: rff_contract<T, 8><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.ard, pb.D, m, pb.theta, Xs, U,
-                                                     Z1, Z2, b.dkpart); break;
+                                                     wt, Z1, Z2, b.dkpart); break;
     case 16: rff_contract<T, 16><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.ard, pb.D, m, pb.theta, Xs,
-                                                       U, Z1, Z2, b.dkpart); break;
+                                                       U, wt, Z1, Z2, b.dkpart); break;
     default: rff_contract<T, 32><<<nblk, 256, 0, st>>>(pb.n, pb.d, pb.ard, pb.D, m, pb.theta, Xs,
-                                                       U, Z1, Z2, b.dkpart); break;
+                                                       U, wt, Z1, Z2, b.dkpart); break;
   }
   GP_LAUNCH_CHECK();
   dk_combine<<<1, 128, 0, st>>>(nblk, 2 * NQ, b.dkpart, EF);
@@ -611,11 +702,12 @@ gp_status feature_terms(const Prob& pb, const void* Xs_, const T* Phi, int64_t l
 }
 
 #define GP_FEAT_INST(T)                                                                        \
-  template gp_status rff_build<T>(const Prob&, const void*, int, const double*, const double*, \
-                                  double*, T*, int64_t, cudaStream_t);                         \
+  template gp_status rff_build<T>(const Prob&, const void*, const FeatSpec&, double*, double*, \
+                                  T*, int64_t, cudaStream_t);                                  \
   template gp_status feature_terms<T>(const Prob&, const void*, const T*, int64_t, int,        \
-                                      const double*, const T*, int64_t, int, const double*,    \
-                                      const PrecBufs&, double*, double*, cudaStream_t);
+                                      const double*, const double*, const T*, int64_t, int,    \
+                                      const double*, const PrecBufs&, double*, double*,        \
+                                      cudaStream_t);
 GP_FEAT_INST(float)
 GP_FEAT_INST(double)
 #undef GP_FEAT_INST

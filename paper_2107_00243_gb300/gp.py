@@ -79,6 +79,8 @@ def load():
         "gp_mll_and_grad": (i32, [P, vp, i32, i32, vp, vp, vp, vp, vp, O, vp, sz, vp]),
         "gp_mll_and_grad_rff": (i32, [P, vp, i32, i32, vp, vp, vp, vp, vp, vp, O, vp, sz,
                                       vp]),
+        "gp_mll_and_grad_qff": (i32, [P, vp, i32, i32, vp, vp, vp, vp, O, vp, sz, vp]),
+        "gp_qff_rule": (i32, [i32, i32, vp, vp]),
         "gp_status_string": (ctypes.c_char_p, [i32]),
         "gp_last_error_message": (ctypes.c_char_p, []),
         "gp_rademacher": (i32, [ctypes.c_uint64, i32, i64, i32, vp, vp]),
@@ -407,6 +409,53 @@ def gp_mll_and_grad_rff(prob, y, m, n_probes, o, eps, g=None, eps_override=None,
                 lib.gp_mll_and_grad_rff(prob.cref(), _ptr(yd), m, n_probes, _ptr(ed), _ptr(gd),
                                         _ptr(eo), _ptr(io), _ptr(out), _ptr(iout),
                                         ctypes.byref(o), _ptr(ws), ws.numel(), _stream()))
+    return st, out, iout
+
+
+def gp_qff_rule(mbar, d):
+    """(U (m, d), W (m,)) numpy arrays: the quadrature rule of gp_mll_and_grad_qff."""
+    import numpy as np
+    lib = load()
+    m = _check("gp_qff_rule", lib.gp_qff_rule(int(mbar), int(d), None, None))
+    U = np.zeros((m, d))
+    W = np.zeros(m)
+    _check("gp_qff_rule", lib.gp_qff_rule(int(mbar), int(d), U.ctypes.data, W.ctypes.data))
+    return U, W
+
+
+def gp_mll_and_grad_qff(prob, y, mbar, n_probes, o, eps_override=None, iters_override=None,
+                        workspace=None, out=None, iout=None):
+    """The estimator with the quadrature Fourier feature preconditioner (RBF kernel,
+    mbar Gauss-Hermite nodes per dimension, k = mbar^d features).  Synchronises.
+    Returns (status, out, iout), laid out as for gp_mll_and_grad with k = mbar^d."""
+    lib = load()
+    t = n_probes + 1
+    k = int(mbar) ** prob.d
+    yd = torch.as_tensor(y).to(device=prob.device, dtype=prob.dtype).contiguous()
+    if out is None:
+        out = torch.empty(out_len(prob.p, n_probes), dtype=torch.float64, device=prob.device)
+    if iout is None:
+        iout = torch.empty(2 + t + max(k, 1), dtype=torch.int32, device=prob.device)
+    eo = io = None
+    if eps_override is not None:
+        eo = torch.as_tensor(eps_override)
+        if tuple(eo.shape) != (k + prob.n, n_probes):
+            raise ValueError(f"eps_override has shape {tuple(eo.shape)}, not "
+                             f"(k + n, n_probes) = {(k + prob.n, n_probes)}")
+        eo = eo.to(device=prob.device, dtype=torch.int8).t().contiguous()
+    if iters_override is not None:
+        io = torch.as_tensor(iters_override, dtype=torch.int32).reshape(-1)
+        if io.numel() != t:
+            raise ValueError(f"iters_override has {io.numel()} entries, not t = {t}")
+        io = io.to(prob.device).contiguous()
+    # the library rejects k above its limit (min(n, 2048)) before touching the workspace
+    ws = (workspace or _WS).get(gp_workspace_size(FN_MLL_AND_GRAD, prob.n, prob.d,
+                                                  min(k, prob.n, 2048), t, prob.precision,
+                                                  o.max_iter), prob.device)
+    st = _check("gp_mll_and_grad_qff",
+                lib.gp_mll_and_grad_qff(prob.cref(), _ptr(yd), int(mbar), n_probes, _ptr(eo),
+                                        _ptr(io), _ptr(out), _ptr(iout), ctypes.byref(o),
+                                        _ptr(ws), ws.numel(), _stream()))
     return st, out, iout
 
 

@@ -6,6 +6,7 @@ GP_ERR_INVALID_ARG and launches nothing).
 """
 import ctypes
 
+import numpy as np
 import pytest
 
 from paper_2107_00243_gb300 import build, gp
@@ -90,3 +91,18 @@ def test_override_marshalling():
     assert gp._piv_override(np.array([5, 0, 2]), 3, "cpu").tolist() == [5, 0, 2]
     with pytest.raises(ValueError):
         gp._piv_override([0, 1, 2, 3, 4], 4, "cpu")
+
+
+@pytest.mark.parametrize("mbar,d", [(2, 1), (4, 1), (16, 1), (64, 1), (6, 2), (8, 3), (4, 5)])
+def test_quadrature_rule_matches_the_oracle(lib, mbar, d):
+    """The host Gauss-Hermite rule of gp_mll_and_grad_qff (Sturm bisection for the nodes,
+    Christoffel numbers for the weights) against the oracle's grid (numpy's hermgauss):
+    same frequencies in the same order, same weights."""
+    from oracle import features
+    U, W = gp.gp_qff_rule(mbar, d)
+    Uo, Wo = features.hermite_grid(mbar, d)
+    assert U.shape == Uo.shape and W.shape == Wo.shape
+    np.testing.assert_allclose(U, Uo, rtol=0, atol=1e-12 * max(1.0, float(np.abs(Uo).max())))
+    np.testing.assert_allclose(W, Wo, rtol=1e-10, atol=1e-300)
+    assert lib.gp_qff_rule(5, 1, None, None) < 0          # odd mbar
+    assert lib.gp_qff_rule(8, 5, None, None) < 0          # 8^5 features exceed the limit

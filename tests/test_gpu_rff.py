@@ -1,5 +1,6 @@
-"""The estimator with the random Fourier feature preconditioner (Tab. 2 "RFF";
-gp_mll_and_grad_rff) against the FP64 oracle through the C ABI.
+"""The estimator with the Fourier feature preconditioners of Tab. 2 against the FP64
+oracle through the C ABI: random features ("RFF"; gp_mll_and_grad_rff) and quadrature
+features of the RBF kernel ("QFF"; gp_mll_and_grad_qff).
 
 Matched runs: the same feature draws (eps, g), the same probe signs (one seed, one
 counter-based generator on both sides) and the oracle's per-column CG iteration counts
@@ -77,3 +78,57 @@ def test_rff_rejects_bad_arguments():
         gp.gp_mll_and_grad_rff(prob, p.y, 8, 2, o, eps, None)
     with pytest.raises(gp.GPError):            # 2m > n
         gp.gp_mll_and_grad_rff(prob, p.y, 51, 2, o, np.zeros((51, 2)), np.ones(51))
+
+
+QFF_CASES = {"ard_d1": (True, 1, 16), "ard_d2": (True, 2, 8), "iso_d3": (False, 3, 4)}
+
+
+@pytest.mark.parametrize("name", sorted(QFF_CASES))
+@pytest.mark.parametrize("prec", [gp.FP64, gp.FP32, gp.BF16])
+def test_qff_estimator_vs_oracle(name, prec):
+    """Quadrature features make P_hat nearly K_hat (CG needs 1-5 iterations), which sets
+    how the two lower precisions are compared:
+    * the MLL is a small difference here (|MLL| ~ 1 % of y^T u and log det), so it is
+      compared on the scale 1/2 (|y^T u| + |log det|) of its components;
+    * FP32: the Woodbury apply sigma^-2 (r - Phi C^-1 Phi^T r) cancels to rounding of
+      eps_32 kappa, kappa = lambda_max(K_hat) / sigma^2 (~1e4 here, eps_32 kappa ~ 8e-4),
+      in every term that uses P^-1 z; the bounds are max(1e-4, 2 eps_32 kappa) on the
+      results and 4 eps_32 kappa on gradient entries;
+    * mixed precision runs the precise split mode (k(r) / s to 22 bits), which is the
+      mode for problems this well preconditioned: fast mode's 11-bit k(r) moved a
+      gradient entry by 5.8e-3 (d = 2)."""
+    ard, d, mbar = QFF_CASES[name]
+    k = mbar ** d
+    p = workloads.random_problem(700, d, kind=kernels.RBF, ard=ard, seed=43, s2=0.05, k=k,
+                                 n_probes=6, tol=TOL[prec][0], max_iter=600)
+    ref = estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, k, p.n_probes, p.tol,
+                                 p.max_iter, seed=7, qff=mbar)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, prec)
+    o = gp.opts(cg_tol=p.tol, max_iter=p.max_iter, seed=7,
+                flags=gp.OPT_SPLIT_P if prec == gp.BF16 else 0)
+    st, out, iout = gp.gp_mll_and_grad_qff(prob, p.y, mbar, p.n_probes, o,
+                                           iters_override=ref["iters"])
+    r = gp.unpack(out, iout, prob.p, p.n_probes, k)
+    assert st >= 0 and r["status"] == 0 and r["rank"] == k
+    np.testing.assert_array_equal(r["iters"], ref["iters"])
+    e = _errors(r, ref)
+    e["mll"] = abs(r["mll"] - ref["mll"]) / (0.5 * (abs(ref["quad"]) + abs(ref["logdet"])))
+    print(name, prec, {kk: f"{v:.1e}" for kk, v in e.items()})
+    tv, tg = TOL[prec][1]
+    if prec == gp.FP32:
+        K_hat = kernels.khat_dense(p.kind, p.X, p.theta, p.ard)
+        kappa = np.linalg.eigvalsh(K_hat)[-1] / p.theta[-1]
+        tv, tg = max(tv, 2 * 2.0 ** -24 * kappa), max(tg, 4 * 2.0 ** -24 * kappa)
+    assert all(e[kk] <= tv for kk in ("mll", "quad", "logdet", "logdetP")), e
+    assert e["grad"] <= tg and e["trP"] <= 3 * tg and e["probeP"] <= 3 * tg, e
+
+
+def test_qff_rejects_other_kernels_and_odd_rules():
+    p = workloads.random_problem(100, 2, kind=kernels.MATERN32, seed=2, k=16, n_probes=2)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, gp.FP64)
+    with pytest.raises(gp.GPError):
+        gp.gp_mll_and_grad_qff(prob, p.y, 4, 2, gp.opts())
+    p = workloads.random_problem(100, 2, kind=kernels.RBF, seed=2, k=16, n_probes=2)
+    prob = gp.Problem(p.X, p.theta, p.kind, p.ard, gp.FP64)
+    with pytest.raises(gp.GPError):
+        gp.gp_mll_and_grad_qff(prob, p.y, 5, 2, gp.opts())
