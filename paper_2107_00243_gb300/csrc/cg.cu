@@ -55,8 +55,8 @@ Dev<T> dev_of(const CgBufs<T>& cb, const T* B, int64_t ldb) {
 
 // Each block owns one contiguous chunk of rows; inside it, warp w handles columns
 // w, w + 8, ... so every column is read as coalesced 128-byte segments and reduced
-// with warp shuffles (no block barrier per column).  The last block to finish
-// combines the per-block partials in block order (deterministic).
+// with warp shuffles (no block barrier per column).  The per-block partials are
+// combined in a fixed order by one block per column (cg_init: by its last block).
 __device__ __forceinline__ void row_chunk(int64_t n, int64_t* r0, int64_t* r1) {
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   *r0 = blockIdx.x * per;
@@ -197,12 +197,12 @@ __global__ void __launch_bounds__(kThreads) cg_init(int64_t n, int t, int max_it
 }
 
 // ---- preconditioner P^-1 R = sigma^-2 (R - L C^-1 L^T R) ------------------------------
-// One application streams L (n x k) twice and does three small steps in between:
+// One application streams L (n x k) twice, with two small steps in between:
 //   (1) S_part[b] = L^T R over the rows of part b               ltr_partial
 //   (2) S = sum of the parts in part order (FP64)                s_reduce
 //   (3) Sp = C^-1 S (FP64)                                       cinv_apply
-//   (4) Z = sigma^-2 (R - L Sp), r^T z per column; the last block
-//       combines the column sums into rho (and beta, or stops a column)   precond_rho
+//   (4) Z = sigma^-2 (R - L Sp), r^T z partials per column          precond_rho
+//   (5) rho (and beta, or a column stops), one block per column       rho_finish
 // The two n-long products keep a register tile per thread and stage tiles of L and of
 // the right-hand sides in shared memory.  The lanes of a warp own pivots (1) or rows
 // (4) 32 apart, so their shared-memory reads of L are conflict-free; the eight warps
