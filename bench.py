@@ -220,18 +220,37 @@ def extrapolate(t_sub, m_sub, m_full, n_full=100000, n_sub=SUBSAMPLE_N, n_hyper=
 
 
 def oracle_small_configs():
-    """Timed, not scaled: the oracle estimator and the exact dense-Cholesky MLL and
-    gradient on the small RBF workload (n = 1,000, d = 3, FP64)."""
-    from oracle import estimator, exact
+    """Oracle timings beside the bench line (about 10 s of host work in all):
+    * timed, not scaled: the oracle estimator and the exact dense-Cholesky MLL and
+      gradient on the small RBF workload (n = 1,000, d = 3) and on a 1,500-point
+      subsample of the Matern-5/2 ARD workload (d = 8, k = 100, l = 50, tol 1e-3);
+    * one kernel product K_hat V of the n = 1e5 RBF workload (t = 33) and of the n = 5e5
+      Matern-3/2 workload (t = 17), timed on 200 and 50 rows (the oracle's own kernel
+      blocks times V) and scaled by the row count to the full product (labelled)."""
+    import numpy as np
+    from oracle import estimator, exact, kernels
     from paper_2107_00243_gb300 import workloads
-    p = workloads.c1_small_rbf()
-    t0 = time.perf_counter()
-    estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, p.k, p.n_probes, p.tol,
-                           p.max_iter, seed=p.seed)
-    t1 = time.perf_counter()
-    exact.exact_mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard)
-    t2 = time.perf_counter()
-    return {"small_rbf_n1000_estimator_s": t1 - t0, "small_rbf_n1000_exact_s": t2 - t1}
+    out = {}
+    for name, p in (("small_rbf_n1000", workloads.c1_small_rbf()),
+                    ("matern52_ard_subsample_n1500",
+                     workloads.subsample(workloads.c2_matern52_ard(), 1500))):
+        t0 = time.perf_counter()
+        estimator.mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard, p.k, p.n_probes, p.tol,
+                               p.max_iter, seed=p.seed)
+        t1 = time.perf_counter()
+        exact.exact_mll_and_grad(p.kind, p.X, p.y, p.theta, p.ard)
+        t2 = time.perf_counter()
+        out[f"{name}_estimator_s"] = t1 - t0
+        out[f"{name}_exact_s"] = t2 - t1
+    for name, p, t, rows in (("rbf_ard_n1e5", workloads.c3_rbf_ard_1e5(), 33, 200),
+                             ("matern32_ard_n5e5", workloads.c4_matern32_5e5(), 17, 50)):
+        V = np.random.default_rng(0).standard_normal((p.n, t))
+        t0 = time.perf_counter()
+        kernels.kernel_block(p.kind, p.X[:rows], p.X, p.theta, p.ard) @ V
+        dt = time.perf_counter() - t0
+        out[f"{name}_product_{rows}_rows_s"] = dt
+        out[f"{name}_product_s_extrapolated"] = dt * p.n / rows
+    return out
 
 
 def run_reference(args, rank, ws, dist):
@@ -867,7 +886,11 @@ def main():
                           f"{SUBSAMPLE_N}-point subsample of the same workload ({t_sub:.2f} s, "
                           f"{m_sub} CG iterations), scaled by (1e5/{SUBSAMPLE_N})^2 and by the "
                           f"product-equivalents per evaluation ({m_full} CG iterations in this "
-                          "run, residual recomputes, 2 x (p-1) derivative passes)"),
+                          "run, residual recomputes, 2 x (p-1) derivative passes). Also timed "
+                          "('timed'): the oracle estimator and the exact MLL + gradient on the "
+                          "small RBF workload and a 1,500-point Matern-5/2 subsample, and row "
+                          "samples of one kernel product at n = 1e5 and n = 5e5 scaled to the "
+                          "whole product"),
                "timed": {"subsample_estimator_s": t_sub, "subsample_n": SUBSAMPLE_N, **small},
                **info}
 
