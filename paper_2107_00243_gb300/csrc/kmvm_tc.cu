@@ -152,11 +152,14 @@ __device__ __forceinline__ void p_from_s(const uint32_t (&v)[32], uint32_t (&pk)
 }
 
 
+// kMaySplit = false: the split flag is known to be off (mode 0), and split mode's code
+// is compiled out, which keeps the fast form's registers free of it.
+template <bool kMaySplit>
 __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
   if (g.gate && *g.gate == 0) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool split = g.err[2] != 0;
+  const bool split = kMaySplit && g.err[2] != 0;
   // split mode: the three-part exponent operands, when the launch's shared memory was
   // sized for them (always, unless the host knew the flag was off or the shape is too
   // wide for them)
@@ -465,36 +468,43 @@ __global__ void __launch_bounds__(kThreads, 1) kmvm_tc_kernel(TcArgs g) {
           // tcgen05.st reads its source registers asynchronously
           tmem_wait_st();
         }
-#pragma unroll 1
-        for (int c = 0; c < 2 && ok && split; ++c) {
-          const int col0 = half * 64 + c * 32;
-          uint32_t v[32];
-          GP_TMEM_LD32(tmem + sbuf * 128 + lane_off + col0, v);
+        if (split) {
+          // split mode, in the same order: both chunks loaded, the S buffer returned to
+          // GEMM1 before any exponential; each chunk's P_hi and P_lo stored as soon as
+          // they are formed (the second chunk reuses the first one's registers only
+          // after its stores have completed)
+          uint32_t v0[32], v1[32];
+          GP_TMEM_LD32(tmem + sbuf * 128 + lane_off + half * 64, v0);
+          GP_TMEM_LD32(tmem + sbuf * 128 + lane_off + half * 64 + 32, v1);
           tmem_wait_ld();
-          if (c == 1) {
-            // both chunks are in registers: release the S buffer for GEMM1
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bars->s_free[sbuf]));
-          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars->s_free[sbuf]));
           if (g.dbg && u == (int)blockIdx.x && blockIdx.x == 0 && j == j0) {
-            for (int q = 0; q < 32; ++q) g.dbg[row * BN + col0 + q] = __uint_as_float(v[q]);
+            for (int q = 0; q < 32; ++q) {
+              g.dbg[row * BN + half * 64 + q] = __uint_as_float(v0[q]);
+              g.dbg[row * BN + half * 64 + 32 + q] = __uint_as_float(v1[q]);
+            }
           }
           uint32_t pk[16], pl[16];
-          if (g.kind == GP_RBF) p_from_s<GP_RBF>(v, pk, pl, split);
-          else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v, pk, pl, split);
-          else if (g.kind == GP_RATQUAD) p_from_s<GP_RATQUAD>(v, pk, pl, split);
-          else p_from_s<GP_MATERN52>(v, pk, pl, split);
-          if (c == 0 && wait_p &&
-              !mbar_wait(smem_u32(&bars->p_free[fb]), p_par, abort, g.err, 33)) {
+          if (g.kind == GP_RBF) p_from_s<GP_RBF>(v0, pk, pl, true);
+          else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v0, pk, pl, true);
+          else if (g.kind == GP_RATQUAD) p_from_s<GP_RATQUAD>(v0, pk, pl, true);
+          else p_from_s<GP_MATERN52>(v0, pk, pl, true);
+          if (wait_p && !mbar_wait(smem_u32(&bars->p_free[fb]), p_par, abort, g.err, 33)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          GP_TMEM_ST16(tmem + 256 + pb * 64 + lane_off + col0 / 2, pk);
-          if (split) GP_TMEM_ST16(tmem + 256 + 64 + lane_off + col0 / 2, pl);
-          // tcgen05.st reads its source registers asynchronously: complete it before
-          // the next chunk reuses them
+          GP_TMEM_ST16(tmem + 256 + pb * 64 + lane_off + half * 32, pk);
+          GP_TMEM_ST16(tmem + 256 + 64 + lane_off + half * 32, pl);
+          tmem_wait_st();          // pk / pl are reused below
+          if (g.kind == GP_RBF) p_from_s<GP_RBF>(v1, pk, pl, true);
+          else if (g.kind == GP_MATERN32) p_from_s<GP_MATERN32>(v1, pk, pl, true);
+          else if (g.kind == GP_RATQUAD) p_from_s<GP_RATQUAD>(v1, pk, pl, true);
+          else p_from_s<GP_MATERN52>(v1, pk, pl, true);
+          GP_TMEM_ST16(tmem + 256 + pb * 64 + lane_off + half * 32 + 16, pk);
+          GP_TMEM_ST16(tmem + 256 + 64 + lane_off + half * 32 + 16, pl);
           tmem_wait_st();
         }
         if (!ok) break;
@@ -880,13 +890,16 @@ gp_status kmvm_tc_cfg(const Prob& pb, const TcBufs& tb, const float* V, int64_t 
   const size_t sm = smem_bytes(kxs, tp, a.nsb, a.nsv);
   static bool attr_set = false;
   if (!attr_set) {
-    GP_CUDA_TRY(cudaFuncSetAttribute(kmvm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemCap));
+    GP_CUDA_TRY(cudaFuncSetAttribute(kmvm_tc_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
+    GP_CUDA_TRY(cudaFuncSetAttribute(kmvm_tc_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
     attr_set = true;
   }
   const int units = nt * a.nchunks;
   const int grid = std::min(units, sm_count());
-  kmvm_tc_kernel<<<grid, kThreads, sm, st>>>(a);
+  if (mode == 0) kmvm_tc_kernel<false><<<grid, kThreads, sm, st>>>(a);
+  else kmvm_tc_kernel<true><<<grid, kThreads, sm, st>>>(a);
   GP_LAUNCH_CHECK();
   tc_reduce_kernel<<<(unsigned)cdiv((int64_t)n * t, 256), 256, 0, st>>>(
       n, npad, t, tp, a.nchunks, tb.part, V, ldv, pb.theta, pb.D, tb.vscale, W, ldw, gate, err);
